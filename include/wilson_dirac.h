@@ -1,0 +1,177 @@
+/*
+ * wilson_dirac.h -- C ABI of the GB300 Wilson-Dirac library.
+ *
+ * Even-odd preconditioned Wilson-Dirac operator ("dslash"), and BiCGstab and
+ * CG-on-the-normal-equations solvers with the reliable-update mixed-precision
+ * scheme of Clark, Babich, Barros, Brower and Rebbi, "Solving lattice QCD
+ * systems of equations using mixed precision solvers on GPUs"
+ * (arXiv:0911.3191).  Section references below are to that paper.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: dims = {X, Y, Z, T}, all even, X >= 2; V = XYZT, Vh = V/2.
+ *   Site (x,y,z,t) has lexicographic index x + X(y + Y(z + Z t)) and parity
+ *   (x+y+z+t) mod 2.  Direction mu = 0,1,2,3 <-> x,y,z,t (gamma_4 is the
+ *   temporal one).  Boundaries are periodic; with t_antiperiodic every hop
+ *   across t = T-1 <-> 0 carries a factor -1 (the paper leaves the boundary
+ *   open; Sec. 4.3 mentions only a boundary surface term).
+ * Host fields (FP64, DeGrand-Rossi spin basis, App. B):
+ *   spinor: [site][spin 4][colour 3][re, im]  = 24 doubles per site
+ *   gauge : [site][mu 4][row 3][col 3][re, im] = 72 doubles per site,
+ *           U_mu(x) is the link from x to x + mu.
+ * Device fields (internal layout, one parity, "single-parity field"): the
+ *   Vh sites of one parity in even-odd order (Sec. 4.1), structure of arrays
+ *   so that consecutive threads read consecutive 16-byte words:
+ *     WD_F64 : 12 arrays of double2  (192 B/site)
+ *     WD_F32 :  6 arrays of float4   ( 96 B/site)
+ *     WD_Q16 :  3 arrays of 8 x int16 codes + 1 array of float norms (Sec. 4.5)
+ *     WD_H16N:  3 arrays of 8 x fp16 + float norms
+ *     WD_B16N:  3 arrays of 8 x bf16 + float norms       (52 B/site each)
+ *   The byte size of one single-parity field is wd_field_bytes(ctx, prec).
+ *   A "full field" is the even field followed by the odd field (2x bytes).
+ *   16-bit storage: per site norm = max |f_k| over the 24 FP32 values f_k;
+ *     Q16 code q_k = rint(f_k * (32767/norm)), value q_k * (norm/32767);
+ *     H16N/B16N hold fp16/bf16(f_k / norm), value h_k * norm; norm 0 -> 0.
+ *   Arithmetic on 16-bit fields is FP32; all global sums are FP64.
+ * Operators (Sec. 3):
+ *   D psi(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                   + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)
+ *   D^dag    = the same with the two projectors exchanged (= gamma5 D gamma5).
+ *   M_kappa  = 1 - kappa D   (= 2 kappa times the paper's M, kappa = 1/(2(4+m)))
+ *   M_hat    = 1 - kappa^2 D_eo D_oe on the even sites.
+ *
+ * Ownership and ordering: the context owns every device buffer it allocates
+ * (gauge copies, solver workspace, staging); the caller owns the buffers it
+ * passes in.  All work is ordered on the context's CUDA stream; calls that
+ * return host results (wd_norm2, wd_solve*, host-side import/export)
+ * synchronise that stream before returning.  A context is used by one host
+ * thread at a time.
+ *
+ * Errors: every call returns a wd_status and never aborts the process;
+ * wd_last_error(ctx) gives a one-line description of the last failure.
+ */
+#ifndef WILSON_DIRAC_H
+#define WILSON_DIRAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_ctx wd_ctx;
+
+typedef enum {
+  WD_OK = 0,
+  WD_ERR_INVALID_ARG = 1, /* bad pointer, size, enum or dims                 */
+  WD_ERR_OOM = 2,         /* device allocation failed                        */
+  WD_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+  WD_ERR_NOT_CONVERGED = 4, /* max_iter reached; x and info are still written */
+  WD_ERR_BREAKDOWN = 5,   /* Krylov breakdown (rho, <r0,v> or <t,t> = 0)      */
+  WD_ERR_NUMERIC = 6,     /* NaN or Inf met in a reduction                    */
+  WD_ERR_TIMEOUT = 7,     /* a bounded device wait gave up                    */
+  WD_ERR_BUDGET = 8,      /* request exceeds the configured memory budget     */
+  WD_ERR_STATE = 9        /* call out of order (e.g. no gauge field loaded)   */
+} wd_status;
+
+typedef enum { WD_F64 = 0, WD_F32 = 1, WD_Q16 = 2, WD_H16N = 3, WD_B16N = 4 } wd_prec;
+typedef enum { WD_BICGSTAB = 0, WD_CGNR = 1 } wd_solver;
+typedef enum { WD_EVEN = 0, WD_ODD = 1 } wd_parity;
+typedef enum { WD_M_FULL = 0, WD_M_SCHUR_EVEN = 1 } wd_operator;
+
+/* Create a context for one lattice (Sec. 4.1: fields split by parity).
+ * dims: {X,Y,Z,T}, each even and >= 2, with Vh < 2^31.  cuda_stream: a
+ * cudaStream_t (NULL = the legacy default stream).  *out receives the handle. */
+wd_status wd_create(wd_ctx **out, const int dims[4], int t_antiperiodic, void *cuda_stream);
+
+/* Free every device buffer the context owns, then the context. NULL is allowed. */
+wd_status wd_destroy(wd_ctx *ctx);
+
+/* Change the stream later work is ordered on. */
+wd_status wd_set_stream(wd_ctx *ctx, void *cuda_stream);
+
+/* Bytes of one single-parity device field of precision prec (0 on bad args). */
+size_t wd_field_bytes(const wd_ctx *ctx, wd_prec prec);
+
+/* Load the gauge field (Sec. 3: SU(3) links U_mu(x)).  U: host layout above,
+ * FP64, on the host (is_device = 0) or the device (is_device = 1).  recon =
+ * 12 stores the first two rows of every link and rebuilds the third as
+ * c = (a x b)^* (App. A.1; exact for SU(3) links); recon = 18 stores all
+ * nine entries (FP64 only).  Lower-precision copies (FP32; Q16 codes
+ * rint(u*32767); fp16; bf16) are derived from the FP64 copy on first use.
+ * Replaces any previous gauge field. */
+wd_status wd_load_gauge(wd_ctx *ctx, const double *U, int is_device, int recon);
+
+/* Host <-> device field transfer with reorder and precision conversion
+ * (Sec. 4.1 layout; Sec. 4.5 16-bit storage; App. B: fields cross in the
+ * DeGrand-Rossi basis).  lex: V x 24 doubles, host (is_device = 0) or device.
+ * Import reads the sites of `parity` from lex and writes the single-parity
+ * device field `field`.  Export writes those sites of lex (others untouched). */
+wd_status wd_field_import(wd_ctx *ctx, void *field, const double *lex, int is_device, wd_parity parity, wd_prec prec);
+wd_status wd_field_export(wd_ctx *ctx, double *lex, const void *field, int is_device, wd_parity parity, wd_prec prec);
+
+/* Dslash (Sec. 3, "the application of D to a spinor field"; Sec. 4):
+ * out = D_{p,1-p} in (dagger: D^dag), where in is the single-parity field of
+ * parity 1-p and out that of parity p = out_parity.  out and in must not
+ * overlap.  Both fields are device fields of precision prec. */
+wd_status wd_dslash(wd_ctx *ctx, void *out, const void *in, wd_parity out_parity, int dagger, wd_prec prec);
+
+/* out = x + a * D_{p,1-p} in  (x of parity p; x may alias out). */
+wd_status wd_dslash_xpay(wd_ctx *ctx, void *out, const void *in, const void *x, double a, wd_parity out_parity,
+                         int dagger, wd_prec prec);
+
+/* Apply the Wilson-Dirac matrix (Sec. 3).  WD_M_FULL: out = M_kappa in on full
+ * fields (even then odd).  WD_M_SCHUR_EVEN: out = M_hat in on even fields
+ * (Sec. 3 Schur complement); the odd temporary is context workspace.
+ * dagger applies M_kappa^dag / M_hat^dag.  out and in must not overlap. */
+wd_status wd_apply_M(wd_ctx *ctx, void *out, const void *in, double kappa, wd_operator which, int dagger,
+                     wd_prec prec);
+
+/* |field|^2 over one single-parity field, summed in FP64 in a fixed order
+ * (Sec. 5.1: global sums in double precision).  Result written to *result. */
+wd_status wd_norm2(wd_ctx *ctx, double *result, const void *field, wd_prec prec);
+
+typedef struct {
+  double tol;          /* stop when |b - M x| <= tol |b| (FP64 true residual)      */
+  double delta;        /* reliable-update threshold, ulp_inner < delta < 1 (Sec. 5.3) */
+  int max_iter;        /* bound on inner iterations (reliable updates included)    */
+  int solver;          /* wd_solver                                                */
+  int inner_precision; /* wd_prec of the Krylov iteration; WD_F64 = pure FP64      */
+  int use_graph;       /* 1: whole solve loop runs as one CUDA graph with device-side
+                          conditional nodes; 0: host-driven loop                   */
+} wd_solve_params;
+
+typedef struct {
+  int iters;                /* k + l of Alg. 2: iterations incl. reliable updates */
+  int reliable_updates;     /* l                                                  */
+  double true_rel_residual; /* |b - M x| / |b|, FP64, recomputed on the full lattice */
+  double iterated_rel_residual; /* last iterated (inner) residual / |b|           */
+  double seconds;           /* wall time of the call                             */
+  int status;               /* wd_status of the solve                            */
+  long long kernel_launches; /* kernels this call ran on the device (graph nodes included) */
+} wd_solve_info;
+
+/* Solve M_kappa x = b (Sec. 5): even-odd Schur system b_hat = b_e + kappa
+ * D_eo b_o, M_hat x_e = b_hat by BiCGstab or CG on M_hat^dag M_hat, then
+ * x_o = b_o + kappa D_oe x_e.  With inner_precision != WD_F64 the iteration
+ * runs in that precision and the reliable-update scheme of Alg. 2 keeps the
+ * solution x, the source and the true residual in FP64 (Sec. 5.3).
+ * x, b: host FP64 fields in the host layout (V x 24 doubles).  On return x
+ * holds the solution and *info is filled even when not converged (status
+ * WD_ERR_NOT_CONVERGED / WD_ERR_BREAKDOWN / WD_ERR_NUMERIC). */
+wd_status wd_solve(wd_ctx *ctx, double *x, const double *b, double kappa, const wd_solve_params *params,
+                   wd_solve_info *info);
+
+/* As wd_solve, with x and b device FP64 full fields in the internal layout
+ * (already resident on the device; no host transfer). */
+wd_status wd_solve_device(wd_ctx *ctx, void *x, const void *b, double kappa, const wd_solve_params *params,
+                          wd_solve_info *info);
+
+/* Description of the last failure on ctx ("" if none); static string for NULL. */
+const char *wd_last_error(const wd_ctx *ctx);
+const char *wd_status_string(wd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WILSON_DIRAC_H */

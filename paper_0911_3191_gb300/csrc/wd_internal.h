@@ -1,0 +1,136 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/wilson_dirac.h"
+#include "wd_device.cuh"
+
+namespace wd {
+
+// Device-resident state of one Krylov solve.  Every scalar of the iteration
+// lives here, written by the finalisers of the fused reductions, so the loop
+// needs no host round trip (Sec. 5: the whole solver runs on the GPU).
+struct SolverCtl {
+  double2 rho, rho_prev, alpha, omega, beta;  // BiCGstab (beta.x also CG's beta)
+  double cg_alpha;   // CG step
+  double rr;         // |r_hat|^2, the iterated residual (CG: normal residual)
+  double rr_prev;    // CG: |r_hat|^2 of the previous iteration
+  double maxr;       // M(r_hat) of Alg. 2: max |r_hat| since the last update
+  double stop2;      // (tol |b|)^2, b the full source
+  double delta;      // reliable-update threshold of Alg. 2
+  double r2_true;    // |b_hat - M_hat x|^2 at the last reliable update
+  double target2;    // CG: current target for the normal residual
+  double neg_kappa2; // -kappa^2
+  double kappa;      // kappa
+  int iter;          // k + l of Alg. 2
+  int max_iter;
+  int updates;       // l of Alg. 2
+  int status;        // wd_status
+  int done;          // 1 once the loop must stop
+  int do_update;     // 1 when this iteration ends with a reliable update
+  int forced;        // the update was forced by apparent convergence or max_iter
+  int in_graph;      // 1: running inside the solver graph (set the conditionals)
+  int loops;         // WHILE-body executions, counted by the loop control kernel
+  int pad;
+  unsigned long long h_update;  // graph conditional handles (used when in_graph)
+  unsigned long long h_loop;
+};
+
+struct Ctx;
+
+// Per-precision operations, one table per storage precision.
+struct PrecOps {
+  wd_prec prec;
+  size_t (*field_bytes)(int stride);
+  // S3: out = D in (plain) or out = x + a D in (xpay); a read from *a_dev if non-null
+  void (*dslash)(const Ctx&, void* out, const void* in, int out_parity, int dagger, cudaStream_t);
+  void (*dslash_xpay)(const Ctx&, void* out, const void* in, const void* x, double a, const double* a_dev,
+                      int out_parity, int dagger, cudaStream_t);
+  // S2 / S13: host-layout FP64 lexicographic field <-> single-parity field
+  void (*import_lex)(const Ctx&, void* field, const double* lex_dev, int parity, cudaStream_t);
+  void (*export_lex)(const Ctx&, double* lex_dev, const void* field, int parity, cudaStream_t);
+  // S10: FP64 single-parity field <-> this precision
+  void (*from_f64)(const Ctx&, void* out, const void* in_f64, cudaStream_t);
+  void (*to_f64)(const Ctx&, void* out_f64, const void* in, cudaStream_t);
+  void (*norm2)(const Ctx&, double* out_dev, const void* field, cudaStream_t);
+  void (*zero)(const Ctx&, void* field, cudaStream_t);
+  // S6 BiCGstab iteration and S9 reliable update with this inner precision
+  void (*bicg_iteration)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  void (*bicg_update)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  void (*bicg_setup)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  // S7 CG on the normal equations, and its reliable update
+  void (*cg_iteration)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  void (*cg_update)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  void (*cg_setup)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  // derive this precision's gauge copy from the FP64 copy
+  void (*gauge_from_f64)(Ctx&, cudaStream_t);
+};
+
+const PrecOps* ops_f64();
+const PrecOps* ops_f32();
+const PrecOps* ops_q16();
+const PrecOps* ops_h16();
+const PrecOps* ops_b16();
+const PrecOps* prec_ops(int prec);
+
+// Workspace of one solve.  FP64 fields (Alg. 2: source b_hat, solution x,
+// residual r, and the odd temporary of the even-odd matrix) plus the inner
+// precision fields (BiCGstab 7, CG 5; Sec. 5.3).
+struct SolveBufs {
+  SolverCtl* ctl;       // device
+  void* b_hat;          // F64 even
+  void* x;              // F64 even, the accumulated solution
+  void* r;              // F64 even (CG: true residual before M_hat^dag)
+  void* tmp64;          // F64 odd
+  void* r_hat;          // inner: r_hat (BiCGstab: also s)
+  void* r_tilde;        // inner: BiCGstab shadow residual
+  void* p;              // inner
+  void* v;              // inner: BiCGstab v, CG w
+  void* t;              // inner: BiCGstab t
+  void* x_hat;          // inner: solution since the last reliable update
+  void* tmp;            // inner odd temporary
+};
+
+struct Ctx {
+  Geom g;
+  int dims[4];
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  // gauge copies (nullptr until loaded / derived)
+  int recon;
+  void* gauge[5];       // by wd_prec: F64 double2; F32 float4; 16-bit: uint4 part
+  void* gauge4[5];      // 16-bit: uint2 part
+  bool gauge_loaded;
+  // reduction scratch
+  RedScratch red;
+  int max_red_blocks;
+  double* scalars;      // small device scratch (API reductions)
+  double* host_pinned;  // pinned host mirror of small results
+  // workspace for the API
+  void* tmp_odd[5];     // odd temporary per precision (apply_M)
+  double* lex_staging;  // V x 24 doubles (host transfers)
+  size_t lex_staging_bytes;
+  // solver workspace
+  SolveBufs sb;
+  int sb_prec, sb_solver;
+  void* sb_block;
+  size_t sb_bytes;
+  void* sb_full[2];     // F64 full fields for host solves (b, x)
+  cudaGraphExec_t graph_exec;
+  cudaGraph_t graph;
+  int graph_prec, graph_solver;
+  unsigned long long graph_hu, graph_hl;  // conditional handles of the graph
+  std::string last_error;
+};
+
+// helpers
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace wd

@@ -1,0 +1,897 @@
+// Kernel templates and per-precision launchers.
+//
+// Each storage precision P (FP64, FP32, Q16, H16N, B16N) instantiates this
+// header once in its own translation unit (wd_prec_*.cu) and exports a
+// PrecOps table.  Kernels:
+//   dslash_kernel : one dslash (Sec. 3-4) with a fused epilogue (xpay, the
+//                   solver vector updates) and fused FP64 reductions (Sec. 5.1)
+//   site_kernel   : BLAS-1, conversions, reorders, with fused FP64 reductions
+// The Krylov scalars stay on the device (SolverCtl), computed by the
+// finalisers of the reductions, so a solver iteration is a fixed sequence of
+// launches that a CUDA graph can replay without host round trips.
+#pragma once
+
+#include "wd_internal.h"
+
+namespace wd {
+
+constexpr int kDslashBlock = 128;
+constexpr int kBlasBlock = 256;
+
+// scalar coefficient: a value, or read from device memory when p != nullptr
+struct Coef {
+  double c;
+  const double* p;
+  __device__ __forceinline__ double get() const { return p ? *p : c; }
+};
+
+// ---------------------------------------------------------- finalisers
+__device__ __forceinline__ void ctl_fail(SolverCtl* ctl, int status) {
+  if (ctl->status == WD_OK) ctl->status = status;
+  ctl->done = 1;
+}
+__device__ __forceinline__ void ctl_set_update(SolverCtl* ctl, int v) {
+  ctl->do_update = v;
+  if (ctl->in_graph) cudaGraphSetConditional((cudaGraphConditionalHandle)ctl->h_update, (unsigned)v);
+}
+
+struct FinStore {
+  double* out;
+  int n;
+  __device__ void operator()(const double* t) const {
+    for (int k = 0; k < n; ++k) out[k] = t[k];
+  }
+};
+
+// BiCGstab: alpha = rho / <r_tilde, v>
+struct FinBicgAlpha {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    double2 rtv = make_double2(t[0], t[1]);
+    if (!cfinite(rtv)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
+    if (rtv.x == 0.0 && rtv.y == 0.0) { ctl_fail(ctl, WD_ERR_BREAKDOWN); return; }
+    ctl->alpha = cdiv(ctl->rho, rtv);
+  }
+};
+
+// BiCGstab: omega = <t, s> / <t, t>
+struct FinBicgOmega {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    double2 ts = make_double2(t[0], t[1]);
+    double tt = t[2];
+    if (!cfinite(ts) || !isfinite(tt)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
+    if (tt == 0.0 || (ts.x == 0.0 && ts.y == 0.0)) { ctl_fail(ctl, WD_ERR_BREAKDOWN); return; }
+    ctl->omega = make_double2(ts.x / tt, ts.y / tt);
+  }
+};
+
+// Reliable-update trigger of Alg. 2: |r_hat_{k+1}| < delta M(r_hat), plus a
+// forced update on apparent convergence (the FP64 true residual then decides)
+// and at max_iter (so x holds everything computed).
+__device__ __forceinline__ void decide_update(SolverCtl* ctl, double rr, double conv2) {
+  const double r = sqrt(rr);
+  const bool conv = rr <= conv2;
+  const bool maxed = ctl->iter >= ctl->max_iter;
+  const bool rel = r < ctl->delta * ctl->maxr;
+  const int upd = (conv || maxed || rel) ? 1 : 0;
+  ctl->forced = (conv || maxed) ? 1 : 0;
+  if (!upd) ctl->maxr = fmax(ctl->maxr, r);
+  ctl_set_update(ctl, upd);
+}
+
+// BiCGstab end of iteration: |r|^2 and rho_new = <r_tilde, r>
+struct FinBicgIter {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    if (ctl->done) { ctl_set_update(ctl, 0); return; }
+    const double rr = t[0];
+    const double2 rho_new = make_double2(t[1], t[2]);
+    ctl->iter += 1;
+    if (!isfinite(rr) || !cfinite(rho_new)) { ctl_fail(ctl, WD_ERR_NUMERIC); ctl_set_update(ctl, 0); return; }
+    ctl->rr = rr;
+    ctl->rho_prev = ctl->rho;
+    ctl->rho = rho_new;
+    ctl->beta = cmul(cdiv(rho_new, ctl->rho_prev), cdiv(ctl->alpha, ctl->omega));
+    decide_update(ctl, (rho_new.x == 0.0 && rho_new.y == 0.0) ? 0.0 : rr, ctl->stop2);
+  }
+};
+
+// BiCGstab reliable update (Alg. 2): t = {|r|^2 FP64, <r_tilde, r_hat>, |r_hat|^2}
+struct FinRelupBicg {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    ctl->updates += 1;
+    const double r2 = t[0];
+    const double2 rho = make_double2(t[1], t[2]);
+    if (!isfinite(r2) || !cfinite(rho)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
+    ctl->r2_true = r2;
+    ctl->rr = t[3];
+    ctl->maxr = sqrt(t[3]);
+    ctl->rho = rho;
+    ctl->beta = cmul(cdiv(rho, ctl->rho_prev), cdiv(ctl->alpha, ctl->omega));
+    if (r2 <= ctl->stop2) { ctl->status = WD_OK; ctl->done = 1; }
+    else if (ctl->iter >= ctl->max_iter) ctl_fail(ctl, WD_ERR_NOT_CONVERGED);
+    else if (rho.x == 0.0 && rho.y == 0.0) ctl_fail(ctl, WD_ERR_BREAKDOWN);
+  }
+};
+
+// BiCGstab setup: r_hat = r_tilde = quantised b_hat; t = {<r_t, r_hat>, |r_hat|^2}
+struct FinBicgSetup {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    ctl->rho = make_double2(t[0], t[1]);
+    ctl->rr = t[2];
+    ctl->maxr = sqrt(t[2]);
+  }
+};
+
+// CG: alpha = |r|^2 / <p, A p>, with <p, M^dag M p> = |M p|^2
+struct FinCgAlpha {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    const double pap = t[0];
+    if (!isfinite(pap)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
+    if (pap <= 0.0) { ctl_fail(ctl, WD_ERR_BREAKDOWN); return; }
+    ctl->cg_alpha = ctl->rr / pap;
+  }
+};
+
+struct FinCgIter {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    if (ctl->done) { ctl_set_update(ctl, 0); return; }
+    const double rr = t[0];
+    ctl->iter += 1;
+    if (!isfinite(rr)) { ctl_fail(ctl, WD_ERR_NUMERIC); ctl_set_update(ctl, 0); return; }
+    ctl->rr_prev = ctl->rr;
+    ctl->rr = rr;
+    ctl->beta = make_double2(rr / ctl->rr_prev, 0.0);
+    decide_update(ctl, rr, ctl->target2);
+  }
+};
+
+// CG reliable update, first half: the FP64 Schur residual r = b_hat - M_hat x
+struct FinRelupCgR {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    ctl->updates += 1;
+    const double r2 = t[0];
+    if (!isfinite(r2)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
+    ctl->r2_true = r2;
+    if (r2 <= ctl->stop2) { ctl->status = WD_OK; ctl->done = 1; return; }
+    if (ctl->iter >= ctl->max_iter) { ctl_fail(ctl, WD_ERR_NOT_CONVERGED); return; }
+    // apparent convergence of the normal residual without the Schur residual
+    // being small enough: tighten the target by the missing factor
+    if (ctl->forced && ctl->rr <= ctl->target2) ctl->target2 *= ctl->stop2 / r2;
+  }
+};
+
+// CG reliable update, second half: r_hat = M_hat^dag r; the next direction
+// uses beta = |r_hat_true|^2 / |r_hat_old|^2 (true residual in the numerator)
+struct FinRelupCgN {
+  SolverCtl* ctl;
+  __device__ void operator()(const double* t) const {
+    const double rr = t[0];
+    if (!isfinite(rr)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
+    ctl->rr = rr;
+    ctl->maxr = sqrt(rr);
+    ctl->beta = make_double2(rr / ctl->rr_prev, 0.0);
+  }
+};
+
+// CG setup: r_hat = M_hat^dag b_hat; t = {|r_hat|^2}
+struct FinCgSetup {
+  SolverCtl* ctl;
+  const double* bhat2;
+  __device__ void operator()(const double* t) const {
+    ctl->rr = t[0];
+    ctl->rr_prev = t[0];
+    ctl->maxr = sqrt(t[0]);
+    ctl->beta = make_double2(0.0, 0.0);
+    // normal-residual target tol |b| |M^dag b_hat| / |b_hat|
+    ctl->target2 = (*bhat2 > 0.0) ? ctl->stop2 * t[0] / *bhat2 : 0.0;
+  }
+};
+
+// ------------------------------------------------------------ epilogues
+// Called once per output site with acc = (D in)(h).
+
+template <class Out>
+struct EpiStore {
+  static constexpr int NRED = 0;
+  Out out;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double*) const { out.store(h, a); }
+};
+
+// out = x + c acc
+template <class Out, class X>
+struct EpiXpay {
+  static constexpr int NRED = 0;
+  Out out;
+  X x;
+  Coef c;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double*) const {
+    R xv[24];
+    x.load(h, xv);
+    const R cc = (R)c.get();
+#pragma unroll
+    for (int k = 0; k < 24; ++k) a[k] = xv[k] + cc * a[k];
+    out.store(h, a);
+  }
+};
+
+// v = x + c acc; reduce <w, v> (v as stored)
+template <class Out, class X, class W, class Fin>
+struct EpiXpayDot {
+  static constexpr int NRED = 2;
+  Out out;
+  X x;
+  W w;
+  Coef c;
+  RedScratch rs;
+  Fin fin;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
+    R xv[24], wv[24];
+    x.load(h, xv);
+    const R cc = (R)c.get();
+#pragma unroll
+    for (int k = 0; k < 24; ++k) a[k] = xv[k] + cc * a[k];
+    out.store_get(h, a);
+    w.load(h, wv);
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re += (double)wv[2 * k] * a[2 * k] + (double)wv[2 * k + 1] * a[2 * k + 1];
+      im += (double)wv[2 * k] * a[2 * k + 1] - (double)wv[2 * k + 1] * a[2 * k];
+    }
+    red[0] += re;
+    red[1] += im;
+  }
+};
+
+// t = s + c acc with s = x; reduce <t, s> and <t, t>
+template <class Out, class X, class Fin>
+struct EpiXpayTS {
+  static constexpr int NRED = 3;
+  Out out;
+  X x;
+  Coef c;
+  RedScratch rs;
+  Fin fin;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
+    R sv[24];
+    x.load(h, sv);
+    const R cc = (R)c.get();
+#pragma unroll
+    for (int k = 0; k < 24; ++k) a[k] = sv[k] + cc * a[k];
+    out.store_get(h, a);
+    double re = 0.0, im = 0.0, tt = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const double tr = a[2 * k], ti = a[2 * k + 1], sr = sv[2 * k], si = sv[2 * k + 1];
+      re += tr * sr + ti * si;
+      im += tr * si - ti * sr;
+      tt += tr * tr + ti * ti;
+    }
+    red[0] += re;
+    red[1] += im;
+    red[2] += tt;
+  }
+};
+
+// v = x + c acc; reduce |v|^2 (v as stored)
+template <class Out, class X, class Fin>
+struct EpiXpayNorm {
+  static constexpr int NRED = 1;
+  Out out;
+  X x;
+  Coef c;
+  RedScratch rs;
+  Fin fin;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
+    R xv[24];
+    x.load(h, xv);
+    const R cc = (R)c.get();
+#pragma unroll
+    for (int k = 0; k < 24; ++k) a[k] = xv[k] + cc * a[k];
+    out.store_get(h, a);
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) n += (double)a[k] * a[k];
+    red[0] += n;
+  }
+};
+
+// CG: q = w + c acc (= M_hat^dag M_hat p); x_hat += alpha p; r_hat -= alpha q;
+// reduce |r_hat|^2.  q is never stored.
+template <class S, class Fin>
+struct EpiCgUpdate {
+  static constexpr int NRED = 1;
+  S w, p, xh, r;
+  Coef c;
+  const SolverCtl* ctl;
+  RedScratch rs;
+  Fin fin;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
+    const R al = (R)ctl->cg_alpha;
+    const R cc = (R)c.get();
+    R wv[24], pv[24], xv[24], rv[24];
+    w.load(h, wv);
+    p.load(h, pv);
+    xh.load(h, xv);
+    r.load(h, rv);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      const R q = wv[k] + cc * a[k];
+      xv[k] += al * pv[k];
+      rv[k] -= al * q;
+    }
+    xh.store(h, xv);
+    r.store_get(h, rv);
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) n += (double)rv[k] * rv[k];
+    red[0] += n;
+  }
+};
+
+// r = b - (x + c acc) in the dslash precision (FP64 for the reliable update);
+// optionally stored; reduce |r|^2
+template <class Out, class B, class X, class Fin>
+struct EpiResid {
+  static constexpr int NRED = 1;
+  Out out;
+  bool store;
+  B b;
+  X x;
+  Coef c;
+  RedScratch rs;
+  Fin fin;
+  template <typename R>
+  __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
+    R bv[24], xv[24];
+    b.load(h, bv);
+    x.load(h, xv);
+    const R cc = (R)c.get();
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      a[k] = bv[k] - (xv[k] + cc * a[k]);
+      n += (double)a[k] * a[k];
+    }
+    if (store) out.store(h, a);
+    red[0] += n;
+  }
+};
+
+// BiCGstab reliable update: r = b_hat - (x + c acc) in FP64, r_hat = quantised
+// r; reduce |r|^2 (FP64), <r_tilde, r_hat>, |r_hat|^2
+template <class RH, class RT, class Fin>
+struct EpiRelupBicg {
+  static constexpr int NRED = 4;
+  SpinorF64 b, x;
+  RH rh;
+  RT rt;
+  Coef c;
+  RedScratch rs;
+  Fin fin;
+  __device__ __forceinline__ void operator()(int h, double (&a)[24], double* red) const {
+    double bv[24], xv[24];
+    b.load(h, bv);
+    x.load(h, xv);
+    const double cc = c.get();
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      a[k] = bv[k] - (xv[k] + cc * a[k]);
+      n += a[k] * a[k];
+    }
+    red[0] += n;
+    rh.store_get(h, a);
+    double wv[24];
+    rt.load(h, wv);
+    double re = 0.0, im = 0.0, m = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re += wv[2 * k] * a[2 * k] + wv[2 * k + 1] * a[2 * k + 1];
+      im += wv[2 * k] * a[2 * k + 1] - wv[2 * k + 1] * a[2 * k];
+      m += a[2 * k] * a[2 * k] + a[2 * k + 1] * a[2 * k + 1];
+    }
+    red[1] += re;
+    red[2] += im;
+    red[3] += m;
+  }
+};
+
+// --------------------------------------------------------------- kernels
+template <bool DAGGER, typename R, class In, class G, class Epi>
+__global__ void __launch_bounds__(kDslashBlock) dslash_kernel(Geom g, In in, G gauge, int parity, Epi epi) {
+  constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
+  double red[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) red[k] = 0.0;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+    R acc[24];
+    dslash_site<DAGGER>(g, in, gauge, h, parity, acc);
+    epi(h, acc, red);
+  }
+  if constexpr (Epi::NRED > 0) grid_reduce<Epi::NRED>(red, epi.rs, epi.fin);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kBlasBlock) site_kernel(int n, Op op) {
+  constexpr int NR = Op::NRED > 0 ? Op::NRED : 1;
+  double red[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) red[k] = 0.0;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) op(h, red);
+  if constexpr (Op::NRED > 0) grid_reduce<Op::NRED>(red, op.rs, op.fin);
+}
+
+__global__ void loop_control_kernel(SolverCtl* ctl);
+
+// ------------------------------------------------------------ BLAS ops
+template <class S, typename R>
+__device__ __forceinline__ void cmac(R (&y)[24], double2 a, const R (&x)[24]) {  // y += a x
+  const R ar = (R)a.x, ai = (R)a.y;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const R xr = x[2 * k], xi = x[2 * k + 1];
+    y[2 * k] += ar * xr - ai * xi;
+    y[2 * k + 1] += ar * xi + ai * xr;
+  }
+}
+
+// BiCGstab: p = r + beta (p - omega v)
+template <class S>
+struct OpBicgP {
+  static constexpr int NRED = 0;
+  S r, p, v;
+  const SolverCtl* ctl;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    using R = typename S::real;
+    const double2 be = ctl->beta, om = ctl->omega;
+    const double2 bo = make_double2(-(be.x * om.x - be.y * om.y), -(be.x * om.y + be.y * om.x));  // -beta omega
+    R rv[24], pv[24], vv[24], o[24];
+    r.load(h, rv);
+    p.load(h, pv);
+    v.load(h, vv);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) o[k] = rv[k];
+    cmac<S>(o, be, pv);
+    cmac<S>(o, bo, vv);
+    p.store(h, o);
+  }
+};
+
+// s = r - alpha v, in place in r
+template <class S>
+struct OpBicgS {
+  static constexpr int NRED = 0;
+  S r, v;
+  const SolverCtl* ctl;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    using R = typename S::real;
+    const double2 al = ctl->alpha;
+    R rv[24], vv[24];
+    r.load(h, rv);
+    v.load(h, vv);
+    cmac<S>(rv, make_double2(-al.x, -al.y), vv);
+    r.store(h, rv);
+  }
+};
+
+// x_hat += alpha p + omega s; r = s - omega t (s lives in r); reduce |r|^2, <r_tilde, r>
+template <class S>
+struct OpBicgFinal {
+  static constexpr int NRED = 3;
+  S xh, p, r, t, rt;
+  const SolverCtl* ctl;
+  RedScratch rs;
+  FinBicgIter fin;
+  __device__ __forceinline__ void operator()(int h, double* red) const {
+    using R = typename S::real;
+    const double2 al = ctl->alpha, om = ctl->omega;
+    R xv[24], pv[24], sv[24], tv[24], wv[24];
+    xh.load(h, xv);
+    p.load(h, pv);
+    r.load(h, sv);
+    t.load(h, tv);
+    cmac<S>(xv, al, pv);
+    cmac<S>(xv, om, sv);
+    xh.store(h, xv);
+    cmac<S>(sv, make_double2(-om.x, -om.y), tv);
+    r.store_get(h, sv);
+    rt.load(h, wv);
+    double n = 0.0, re = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const double a = sv[2 * k], b = sv[2 * k + 1], wr = wv[2 * k], wi = wv[2 * k + 1];
+      n += a * a + b * b;
+      re += wr * a + wi * b;
+      im += wr * b - wi * a;
+    }
+    red[0] += n;
+    red[1] += re;
+    red[2] += im;
+  }
+};
+
+// CG: p = r + beta p
+template <class S>
+struct OpCgP {
+  static constexpr int NRED = 0;
+  S r, p;
+  const SolverCtl* ctl;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    using R = typename S::real;
+    const R be = (R)ctl->beta.x;
+    R rv[24], pv[24];
+    r.load(h, rv);
+    p.load(h, pv);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) pv[k] = rv[k] + be * pv[k];
+    p.store(h, pv);
+  }
+};
+
+// Alg. 2: x = x + x_hat (FP64 accumulation), x_hat = 0
+template <class S>
+struct OpAccumulate {
+  static constexpr int NRED = 0;
+  SpinorF64 x;
+  S xh;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    double xv[24], hv[24];
+    x.load(h, xv);
+    xh.load(h, hv);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      xv[k] += hv[k];
+      hv[k] = 0.0;
+    }
+    x.store(h, xv);
+    xh.store(h, hv);
+  }
+};
+
+// out = in with precision conversion
+template <class Out, class In>
+struct OpConvert {
+  static constexpr int NRED = 0;
+  Out out;
+  In in;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    using R = typename In::real;
+    R v[24];
+    in.load(h, v);
+    out.store(h, v);
+  }
+};
+
+// out1 = out2 = quantised in; reduce <out, out> (complex) and |out|^2
+template <class Out, class In, class Fin>
+struct OpQuantDup {
+  static constexpr int NRED = 3;
+  Out out1, out2;
+  In in;
+  RedScratch rs;
+  Fin fin;
+  __device__ __forceinline__ void operator()(int h, double* red) const {
+    double v[24], v2[24];
+    in.load(h, v);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) v2[k] = v[k];
+    out1.store_get(h, v);
+    out2.store(h, v2);  // same source, same encoding: identical bits
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) n += v[k] * v[k];
+    red[0] += n;
+    red[2] += n;
+  }
+};
+
+template <class S>
+struct OpNorm2 {
+  static constexpr int NRED = 1;
+  S in;
+  RedScratch rs;
+  FinStore fin;
+  __device__ __forceinline__ void operator()(int h, double* red) const {
+    using R = typename S::real;
+    R v[24];
+    in.load(h, v);
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) n += (double)v[k] * v[k];
+    red[0] += n;
+  }
+};
+
+template <class S>
+struct OpZero {
+  static constexpr int NRED = 0;
+  S out;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    float z[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) z[k] = 0.f;
+    out.store(h, z);
+  }
+};
+
+// host layout (lexicographic FP64, [site][spin][colour][re,im]) <-> field
+template <class S>
+struct OpImport {
+  static constexpr int NRED = 0;
+  Geom g;
+  S out;
+  const double* lex;
+  int parity;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    int x, y, z, t;
+    site_coords(g, h, parity, x, y, z, t);
+    const size_t s = (size_t)x + (size_t)g.X * (y + (size_t)g.Y * (z + (size_t)g.Z * t));
+    double v[24];
+    const double2* src = reinterpret_cast<const double2*>(lex + 24 * s);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 d = src[k];
+      v[2 * k] = d.x;
+      v[2 * k + 1] = d.y;
+    }
+    out.store(h, v);
+  }
+};
+
+template <class S>
+struct OpExport {
+  static constexpr int NRED = 0;
+  Geom g;
+  S in;
+  double* lex;
+  int parity;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    using R = typename S::real;
+    int x, y, z, t;
+    site_coords(g, h, parity, x, y, z, t);
+    const size_t s = (size_t)x + (size_t)g.X * (y + (size_t)g.Y * (z + (size_t)g.Z * t));
+    R v[24];
+    in.load(h, v);
+    double2* dst = reinterpret_cast<double2*>(lex + 24 * s);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+  }
+};
+
+// ---------------------------------------------------------------- views
+template <int P>
+struct Tr;
+
+template <>
+struct Tr<WD_F64> {
+  using S = SpinorF64;
+  using G = GaugeF64;
+  using R = double;
+  static size_t bytes(int stride) { return align256(192 * (size_t)stride); }
+  static S view(const void* p, const Geom& g) { return S{(double2*)p, g.stride}; }
+  static G gauge(const Ctx& c) { return G{(const double2*)c.gauge[WD_F64], c.g.stride, c.recon}; }
+};
+template <>
+struct Tr<WD_F32> {
+  using S = SpinorF32;
+  using G = GaugeF32;
+  using R = float;
+  static size_t bytes(int stride) { return align256(96 * (size_t)stride); }
+  static S view(const void* p, const Geom& g) { return S{(float4*)p, g.stride}; }
+  static G gauge(const Ctx& c) { return G{(const float4*)c.gauge[WD_F32], c.g.stride}; }
+};
+template <Fmt16 F, int P>
+struct Tr16 {
+  using S = Spinor16<F>;
+  using G = Gauge16<F>;
+  using R = float;
+  static size_t bytes(int stride) { return align256(48 * (size_t)stride) + align256(4 * (size_t)stride); }
+  static S view(const void* p, const Geom& g) {
+    return S{(uint4*)p, (float*)((char*)p + align256(48 * (size_t)g.stride)), g.stride};
+  }
+  static G gauge(const Ctx& c) { return G{(const uint4*)c.gauge[P], (const uint2*)c.gauge4[P], c.g.stride}; }
+};
+template <>
+struct Tr<WD_Q16> : Tr16<Fmt16::Q16, WD_Q16> {};
+template <>
+struct Tr<WD_H16N> : Tr16<Fmt16::H16, WD_H16N> {};
+template <>
+struct Tr<WD_B16N> : Tr16<Fmt16::B16, WD_B16N> {};
+
+// ------------------------------------------------------------ launchers
+inline int dslash_grid(const Ctx& c) {
+  int b = (c.g.Vh + kDslashBlock - 1) / kDslashBlock;
+  return b < c.num_sms * 16 ? b : c.num_sms * 16;
+}
+inline int blas_grid(const Ctx& c, int n) {
+  int b = (n + kBlasBlock - 1) / kBlasBlock;
+  return b < c.num_sms * 8 ? b : c.num_sms * 8;
+}
+
+template <typename R, class In, class G, class Epi>
+void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int dagger, const Epi& epi,
+                   cudaStream_t s) {
+  const int grid = dslash_grid(c);
+  if (dagger)
+    dslash_kernel<true, R, In, G, Epi><<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
+  else
+    dslash_kernel<false, R, In, G, Epi><<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
+}
+
+template <class Op>
+void launch_sites(const Ctx& c, int n, const Op& op, cudaStream_t s) {
+  site_kernel<Op><<<blas_grid(c, n), kBlasBlock, 0, s>>>(n, op);
+}
+
+// Per-precision implementation.  Inner fields are of precision P; the
+// reliable update runs the FP64 dslash with P-precision outputs.
+template <int P>
+struct Impl {
+  using T = Tr<P>;
+  using S = typename T::S;
+  using R = typename T::R;
+  using T64 = Tr<WD_F64>;
+
+  static size_t field_bytes(int stride) { return T::bytes(stride); }
+
+  static void dslash(const Ctx& c, void* out, const void* in, int parity, int dagger, cudaStream_t s) {
+    EpiStore<S> e{T::view(out, c.g)};
+    launch_dslash<R>(c, T::view(in, c.g), T::gauge(c), parity, dagger, e, s);
+  }
+  static void dslash_xpay(const Ctx& c, void* out, const void* in, const void* x, double a, const double* a_dev,
+                          int parity, int dagger, cudaStream_t s) {
+    EpiXpay<S, S> e{T::view(out, c.g), T::view(x, c.g), Coef{a, a_dev}};
+    launch_dslash<R>(c, T::view(in, c.g), T::gauge(c), parity, dagger, e, s);
+  }
+  static void import_lex(const Ctx& c, void* field, const double* lex, int parity, cudaStream_t s) {
+    launch_sites(c, c.g.Vh, OpImport<S>{c.g, T::view(field, c.g), lex, parity}, s);
+  }
+  static void export_lex(const Ctx& c, double* lex, const void* field, int parity, cudaStream_t s) {
+    launch_sites(c, c.g.Vh, OpExport<S>{c.g, T::view(field, c.g), lex, parity}, s);
+  }
+  static void from_f64(const Ctx& c, void* out, const void* in, cudaStream_t s) {
+    launch_sites(c, c.g.Vh, OpConvert<S, SpinorF64>{T::view(out, c.g), T64::view(in, c.g)}, s);
+  }
+  static void to_f64(const Ctx& c, void* out, const void* in, cudaStream_t s) {
+    launch_sites(c, c.g.Vh, OpConvert<SpinorF64, S>{T64::view(out, c.g), T::view(in, c.g)}, s);
+  }
+  static void norm2(const Ctx& c, double* out, const void* field, cudaStream_t s) {
+    launch_sites(c, c.g.Vh, OpNorm2<S>{T::view(field, c.g), c.red, FinStore{out, 1}}, s);
+  }
+  static void zero(const Ctx& c, void* field, cudaStream_t s) {
+    launch_sites(c, c.g.Vh, OpZero<S>{T::view(field, c.g)}, s);
+  }
+
+  // ---- BiCGstab on M_hat (Sec. 5.1), inner precision P
+  static void bicg_setup(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    using Q = OpQuantDup<S, SpinorF64, FinBicgSetup>;
+    launch_sites(c, c.g.Vh, Q{T::view(b.r_hat, c.g), T::view(b.r_tilde, c.g), T64::view(b.b_hat, c.g), c.red,
+                               FinBicgSetup{b.ctl}}, s);
+    zero(c, b.p, s);
+    zero(c, b.v, s);
+    zero(c, b.x_hat, s);
+  }
+  static void bicg_iteration(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    const Geom& g = c.g;
+    const Coef nk2{0.0, &b.ctl->neg_kappa2};
+    // p = r + beta (p - omega v)
+    launch_sites(c, g.Vh, OpBicgP<S>{T::view(b.r_hat, g), T::view(b.p, g), T::view(b.v, g), b.ctl}, s);
+    // v = M_hat p, alpha = rho / <r_tilde, v>
+    dslash(c, b.tmp, b.p, 1, 0, s);
+    {
+      EpiXpayDot<S, S, S, FinBicgAlpha> e{T::view(b.v, g), T::view(b.p, g), T::view(b.r_tilde, g), nk2, c.red,
+                                          FinBicgAlpha{b.ctl}};
+      launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 0, e, s);
+    }
+    // s = r - alpha v
+    launch_sites(c, g.Vh, OpBicgS<S>{T::view(b.r_hat, g), T::view(b.v, g), b.ctl}, s);
+    // t = M_hat s, omega = <t, s> / <t, t>
+    dslash(c, b.tmp, b.r_hat, 1, 0, s);
+    {
+      EpiXpayTS<S, S, FinBicgOmega> e{T::view(b.t, g), T::view(b.r_hat, g), nk2, c.red, FinBicgOmega{b.ctl}};
+      launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 0, e, s);
+    }
+    // x_hat += alpha p + omega s, r = s - omega t, |r|^2, rho = <r_tilde, r>
+    launch_sites(c, g.Vh,
+                 OpBicgFinal<S>{T::view(b.x_hat, g), T::view(b.p, g), T::view(b.r_hat, g), T::view(b.t, g),
+                                T::view(b.r_tilde, g), b.ctl, c.red, FinBicgIter{b.ctl}},
+                 s);
+  }
+  // Alg. 2 reliable update: x += x_hat, x_hat = 0, r = b_hat - M_hat x (FP64),
+  // r_hat = r (quantised), rho = <r_tilde, r_hat>
+  static void bicg_update(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    const Geom& g = c.g;
+    launch_sites(c, g.Vh, OpAccumulate<S>{T64::view(b.x, g), T::view(b.x_hat, g)}, s);
+    EpiStore<SpinorF64> e0{T64::view(b.tmp64, g)};
+    launch_dslash<double>(c, T64::view(b.x, g), T64::gauge(c), 1, 0, e0, s);
+    EpiRelupBicg<S, S, FinRelupBicg> e1{T64::view(b.b_hat, g), T64::view(b.x, g), T::view(b.r_hat, g),
+                                         T::view(b.r_tilde, g), Coef{0.0, &b.ctl->neg_kappa2}, c.red,
+                                         FinRelupBicg{b.ctl}};
+    launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 0, e1, s);
+  }
+
+  // ---- CG on M_hat^dag M_hat (Sec. 5.1), inner precision P
+  static void cg_setup(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    const Geom& g = c.g;
+    // r_hat = M_hat^dag b_hat  (FP64 dslash, output quantised)
+    EpiStore<SpinorF64> e0{T64::view(b.tmp64, g)};
+    launch_dslash<double>(c, T64::view(b.b_hat, g), T64::gauge(c), 1, 1, e0, s);
+    EpiXpayNorm<S, SpinorF64, FinCgSetup> e1{T::view(b.r_hat, g), T64::view(b.b_hat, g),
+                                             Coef{0.0, &b.ctl->neg_kappa2}, c.red,
+                                             FinCgSetup{b.ctl, c.scalars + 2}};
+    launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 1, e1, s);
+    zero(c, b.p, s);
+    zero(c, b.x_hat, s);
+  }
+  static void cg_iteration(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    const Geom& g = c.g;
+    const Coef nk2{0.0, &b.ctl->neg_kappa2};
+    launch_sites(c, g.Vh, OpCgP<S>{T::view(b.r_hat, g), T::view(b.p, g), b.ctl}, s);
+    // w = M_hat p, alpha = |r|^2 / |w|^2
+    dslash(c, b.tmp, b.p, 1, 0, s);
+    {
+      EpiXpayNorm<S, S, FinCgAlpha> e{T::view(b.v, g), T::view(b.p, g), nk2, c.red, FinCgAlpha{b.ctl}};
+      launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 0, e, s);
+    }
+    // q = M_hat^dag w; x_hat += alpha p; r -= alpha q; |r|^2
+    dslash(c, b.tmp, b.v, 1, 1, s);
+    {
+      EpiCgUpdate<S, FinCgIter> e{T::view(b.v, g), T::view(b.p, g), T::view(b.x_hat, g), T::view(b.r_hat, g),
+                                  nk2, b.ctl, c.red, FinCgIter{b.ctl}};
+      launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 1, e, s);
+    }
+  }
+  static void cg_update(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    const Geom& g = c.g;
+    const Coef nk2{0.0, &b.ctl->neg_kappa2};
+    launch_sites(c, g.Vh, OpAccumulate<S>{T64::view(b.x, g), T::view(b.x_hat, g)}, s);
+    // r = b_hat - M_hat x  (FP64, stored)
+    EpiStore<SpinorF64> e0{T64::view(b.tmp64, g)};
+    launch_dslash<double>(c, T64::view(b.x, g), T64::gauge(c), 1, 0, e0, s);
+    EpiResid<SpinorF64, SpinorF64, SpinorF64, FinRelupCgR> e1{
+        T64::view(b.r, g), true, T64::view(b.b_hat, g), T64::view(b.x, g), nk2, c.red, FinRelupCgR{b.ctl}};
+    launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 0, e1, s);
+    // r_hat = M_hat^dag r (quantised)
+    launch_dslash<double>(c, T64::view(b.r, g), T64::gauge(c), 1, 1, e0, s);
+    EpiXpayNorm<S, SpinorF64, FinRelupCgN> e2{T::view(b.r_hat, g), T64::view(b.r, g), nk2, c.red,
+                                              FinRelupCgN{b.ctl}};
+    launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 1, e2, s);
+  }
+
+  static PrecOps make() {
+    PrecOps o{};
+    o.prec = (wd_prec)P;
+    o.field_bytes = &field_bytes;
+    o.dslash = &dslash;
+    o.dslash_xpay = &dslash_xpay;
+    o.import_lex = &import_lex;
+    o.export_lex = &export_lex;
+    o.from_f64 = &from_f64;
+    o.to_f64 = &to_f64;
+    o.norm2 = &norm2;
+    o.zero = &zero;
+    o.bicg_iteration = &bicg_iteration;
+    o.bicg_update = &bicg_update;
+    o.bicg_setup = &bicg_setup;
+    o.cg_iteration = &cg_iteration;
+    o.cg_update = &cg_update;
+    o.cg_setup = &cg_setup;
+    return o;
+  }
+};
+
+}  // namespace wd
