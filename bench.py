@@ -354,6 +354,29 @@ def dslash_sweep(torch, args):
     return out
 
 
+def run_dslash_only(args):
+    import torch
+
+    import lattice_inputs as li
+    import paper_0911_3191_gb300 as wdp
+    dims = tuple(int(x) for x in args.sweep_dims.split(","))
+    prec = wdp.PREC_BY_NAME[args.dslash_only]
+    wd = wdp.WilsonDirac(dims)
+    wd.load_gauge(li.gauge(dims, 0.3, 1002))
+    fin = wd.new_field(prec)
+    fin.zero_()
+    fout = wd.new_field(prec)
+    for _ in range(args.warmup + args.steps):
+        wd.dslash(fout, fin, wdp.EVEN, False, prec)
+    torch.cuda.synchronize()
+    t = time_dslash(wd, torch, prec, max(1, args.steps))
+    vh = li.volume(dims) // 2
+    gbs = BYTES_PER_SITE[prec] * vh / t / 1e9
+    print(json.dumps({"dslash": args.dslash_only, "lattice": "x".join(map(str, dims)), "us": round(t * 1e6, 2),
+                      "GB/s": round(gbs, 1), "frac": round(gbs / peaks()[0], 4)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,7 +390,11 @@ def main():
     ap.add_argument("--sweep-dims", default="64,64,64,128")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--dslash-only", default=None, choices=["f64", "f32", "q16", "h16n", "b16n"],
+                    help="time only the dslash of one precision on --sweep-dims (profiling case)")
     args = ap.parse_args()
+    if args.dslash_only:
+        return run_dslash_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
