@@ -167,6 +167,30 @@ wd_status wd_solve(wd_ctx *ctx, double *x, const double *b, double kappa, const 
 wd_status wd_solve_device(wd_ctx *ctx, void *x, const void *b, double kappa, const wd_solve_params *params,
                           wd_solve_info *info);
 
+/* |field|^2 of one single-parity device field, in FP64, for callers that
+ * cannot allocate device memory.  (The paper has no counterpart; this is a
+ * service of the library.)  Such callers -- code whose host framework owns all
+ * device memory through its own pool and forbids allocations on its hot path,
+ * or code about to capture its work into a CUDA graph -- cannot create a
+ * wd_ctx, because wd_create allocates.  This call needs no context and
+ * allocates nothing: the reduction's scratch (one partial sum per block plus a
+ * ticket counter) is a static device array of the library, about 512 KB on
+ * every GPU that loads it, kept until the process exits.
+ *   result : DEVICE pointer to one double, written on `cuda_stream`; the call
+ *            returns without synchronising, so read it after the stream.
+ *   field  : single-parity device field of precision prec for lattice dims
+ *            (layout as above).
+ *   dims   : {X,Y,Z,T}, each even and >= 2, with at most 16,777,216 sites per
+ *            parity (the scratch holds 65,536 partial sums of 256 sites);
+ *            larger lattices are rejected with WD_ERR_INVALID_ARG.
+ *   err    : optional buffer of err_len bytes for a one-line error message.
+ * The first call on a device looks up the scratch address on that device;
+ * make it before any stream capture.  All calls share the scratch: calls that
+ * overlap on the GPU (other streams, other host threads) race and must not be
+ * issued. */
+wd_status wd_norm2_noalloc(double *result, const void *field, const int dims[4], wd_prec prec, void *cuda_stream,
+                           char *err, size_t err_len);
+
 /* Description of the last failure on ctx ("" if none); static string for NULL. */
 const char *wd_last_error(const wd_ctx *ctx);
 const char *wd_status_string(wd_status s);

@@ -96,7 +96,8 @@ def exported_symbols():
     lib = load_library()
     return [n for n in ("wd_create", "wd_destroy", "wd_set_stream", "wd_field_bytes", "wd_load_gauge",
                         "wd_field_import", "wd_field_export", "wd_dslash", "wd_dslash_xpay", "wd_apply_M", "wd_norm2",
-                        "wd_solve", "wd_solve_device", "wd_last_error", "wd_status_string") if hasattr(lib, n)]
+                        "wd_solve", "wd_solve_device", "wd_norm2_noalloc", "wd_last_error", "wd_status_string")
+            if hasattr(lib, n)]
 
 
 def _ptr(a) -> int:
