@@ -228,14 +228,15 @@ def run_ours(args):
     U = li.gauge(dims, W["eps"], W["gauge_seed"])
     b = li.gaussian_spinor(dims, W["source_seed"])
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(U)
+    wd.load_gauge(U, recon=args.recon)
     s = wd.stream
     fb = wd.upload(b, wdp.F64)
     fx = wd.new_field(wdp.F64, 2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
     def solve(prec):
-        return wd.solve_device(fx, fb, kappa, tol=tol, delta=delta, solver=solver, inner_precision=prec)
+        return wd.solve_device(fx, fb, kappa, tol=tol, delta=delta, solver=solver, inner_precision=prec,
+                               use_graph=not args.host_loop)
 
     for _ in range(args.warmup):
         solve(inner)
@@ -306,6 +307,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(1000 * t_total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.inner + "+f64", "data": "synthetic",
             "config": {"workload": W["workload"], "lattice": "24x24x24x64", "solver": args.solver,
+                       "fp64_link_reals": args.recon, "loop": "host" if args.host_loop else "cuda-graph",
                        "inner_precision": args.inner, "parallelism": f"replicas{ws}",
                        "l2": "flushed between timed solves (256 MB write); inputs (FP64 gauge 340 MB) exceed L2"},
             "solve": {"iters": r0.iters, "reliable_updates": r0.reliable_updates,
@@ -339,7 +341,7 @@ def dslash_sweep(torch, args):
     U = li.gauge(dims, 0.3, 1002)
     gen_s = time.perf_counter() - t0
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(U)
+    wd.load_gauge(U, recon=args.recon)
     del U
     hbm, src = peaks()
     out = {"lattice": "x".join(map(str, dims)), "gauge_gen_s": round(gen_s, 1)}
@@ -362,7 +364,7 @@ def run_dslash_only(args):
     dims = tuple(int(x) for x in args.sweep_dims.split(","))
     prec = wdp.PREC_BY_NAME[args.dslash_only]
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(li.gauge(dims, 0.3, 1002))
+    wd.load_gauge(li.gauge(dims, 0.3, 1002), recon=args.recon)
     fin = wd.new_field(prec)
     fin.zero_()
     fout = wd.new_field(prec)
@@ -374,6 +376,155 @@ def run_dslash_only(args):
     gbs = BYTES_PER_SITE[prec] * vh / t / 1e9
     print(json.dumps({"dslash": args.dslash_only, "lattice": "x".join(map(str, dims)), "us": round(t * 1e6, 2),
                       "GB/s": round(gbs, 1), "frac": round(gbs / peaks()[0], 4)}))
+    return 0
+
+
+def run_batch(args):
+    """Batched multi-RHS solve: 12 point-source spin-colour right-hand sides x
+    4 kappa = 48 systems on a 32^3 x 64 lattice (links exp(0.3 i H)), Q16 inner
+    BiCGstab with FP64 reliable updates to 1e-12, in one batched graph; timed
+    against the same systems solved one at a time."""
+    import numpy as np
+    import torch
+
+    import lattice_inputs as li
+    import paper_0911_3191_gb300 as wdp
+    dims = (32, 32, 32, 64)
+    kappas = [0.118, 0.12, 0.122, 0.124]
+    inner = wdp.PREC_BY_NAME[args.inner]
+    wd = wdp.WilsonDirac(dims)
+    wd.load_gauge(li.gauge(dims, 0.3, 1003), recon=args.recon)
+    V = li.volume(dims)
+    pts = [(s, c) for s in range(4) for c in range(3)]
+    n = len(pts) * len(kappas)
+    full = 2 * wd.field_bytes(wdp.F64)
+    fb = wd.new_field(wdp.F64, 2 * n)
+    host = np.zeros((V, 4, 3), dtype=np.complex128)
+    ks = []
+    r = 0
+    for k in kappas:
+        for (sp, co) in pts:
+            host[0, sp, co] = 1.0
+            f = fb[r * full:(r + 1) * full]
+            wd.field_import(f[:full // 2], host, wdp.EVEN, wdp.F64)
+            wd.field_import(f[full // 2:], host, wdp.ODD, wdp.F64)
+            host[0, sp, co] = 0.0
+            ks.append(k)
+            r += 1
+    fx = wd.new_field(wdp.F64, 2 * n)
+    s = wd.stream
+    t0 = time.perf_counter()
+    infos = wd.solve_batch_device(fx, fb, ks, tol=1e-12, inner_precision=inner)  # includes the autotuning
+    first_s = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        wd.solve_batch_device(fx, fb, ks, tol=1e-12, inner_precision=inner)
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            infos = wd.solve_batch_device(fx, fb, ks, tol=1e-12, inner_precision=inner)
+            e1.record(s)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1000.0)
+    assert all(i.status == 0 and i.true_rel_residual <= 1e-12 for i in infos), infos
+    t_batch = statistics.mean(times)
+    # the same systems one at a time (a sample of 8, scaled to 48)
+    sample = list(range(0, n, n // 8))
+    t_single = 0.0
+    fx1 = wd.new_field(wdp.F64, 2)
+    for q in sample:
+        wd.solve_device(fx1, fb[q * full:(q + 1) * full], ks[q], tol=1e-12, inner_precision=inner)  # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        r1 = wd.solve_device(fx1, fb[q * full:(q + 1) * full], ks[q], tol=1e-12, inner_precision=inner)
+        e1.record(s)
+        e1.synchronize()
+        assert r1.status == 0
+        t_single += e0.elapsed_time(e1) / 1000.0
+    t_single *= n / len(sample)
+    print(json.dumps({"batch": "32x32x32x64, 12 point sources x 4 kappa", "n_systems": n, "inner": args.inner,
+                      "fp64_link_reals": args.recon, "s_per_batched_solve": round(t_batch, 4),
+                      "systems_per_s": round(n / t_batch, 3), "s_first_call_incl_tuning": round(first_s, 3),
+                      "s_one_at_a_time_est": round(t_single, 4), "batch_speedup": round(t_single / t_batch, 3),
+                      "iters": [i.iters for i in infos], "reliable_updates": [i.reliable_updates for i in infos],
+                      "max_true_rel_residual": max(i.true_rel_residual for i in infos), "clocks": clk.summary()}))
+    return 0
+
+
+def run_serve(args):
+    """Serving stream: Poisson arrivals (exponential gaps, seed 3000) at 200/s
+    of solve requests on 8 resident gauge fields (2 per volume: 16^3x32,
+    24^3x48, 32^3x64, 48^3x96; links exp(0.3 i H)), kappa ~ U[0.115, 0.124],
+    tol in {1e-8, 1e-10, 1e-12}, device-memory budget 80 GB, continuous
+    batching through wd_server_*.  Each volume's requests share one Gaussian
+    source and one host solution buffer (the client does not keep every
+    solution); every request's FP64 true residual is reported by the server."""
+    import numpy as np
+
+    import lattice_inputs as li
+    import paper_0911_3191_gb300 as wdp
+    vols = [(16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64), (48, 48, 48, 96)]
+    rng = np.random.default_rng(3000)
+    n = args.serve_requests
+    gaps = rng.exponential(1.0 / 200.0, size=n)
+    arrival = np.cumsum(gaps) - gaps[0]
+    vol_idx = rng.integers(0, 4, size=n)
+    field_idx = rng.integers(0, 2, size=n)
+    kappas = rng.uniform(0.115, 0.124, size=n)
+    tols = np.array([1e-8, 1e-10, 1e-12])[rng.integers(0, 3, size=n)]
+    inner = wdp.PREC_BY_NAME[args.inner]
+    srv = wdp.Server(budget_bytes=80 * 1000**3, max_slots=args.serve_slots, iters_per_step=args.serve_iters,
+                     inner_precision=inner, delta=0.1)
+    gids, srcs, outs = {}, {}, {}
+    t0 = time.perf_counter()
+    for v, dims in enumerate(vols):
+        for f in range(2):
+            gids[(v, f)] = srv.add_gauge(dims, li.gauge(dims, 0.3, 1100 + 2 * v + f), recon=args.recon)
+        srcs[v] = li.gaussian_spinor(dims, 2400 + v)
+        outs[v] = np.zeros_like(srcs[v])
+    setup_s = time.perf_counter() - t0
+    pending, lat, infos = {}, [], []
+    nxt = 0
+    start = time.perf_counter()
+    with ClockSampler(0) as clk:
+        while nxt < n or pending:
+            now = time.perf_counter() - start
+            while nxt < n and arrival[nxt] <= now:
+                v = int(vol_idx[nxt])
+                rid = srv.submit(gids[(v, int(field_idx[nxt]))], srcs[v], float(kappas[nxt]), float(tols[nxt]),
+                                 x=outs[v])
+                pending[rid] = (nxt, float(tols[nxt]))
+                nxt += 1
+            if not pending:
+                time.sleep(max(0.0, min(arrival[nxt] - now, 0.01)))
+                continue
+            srv.step()
+            tnow = time.perf_counter() - start
+            for rid in list(pending):
+                f, res, _ = srv.poll(rid)
+                if f:
+                    i, tol = pending.pop(rid)
+                    lat.append(tnow - arrival[i])
+                    infos.append((res, tol, int(vol_idx[i])))
+    makespan = time.perf_counter() - start
+    ok = sum(1 for r, tol, _ in infos if r.status == 0 and r.true_rel_residual <= tol)
+    lat_a = np.array(lat)
+    per_vol = {}
+    for v, dims in enumerate(vols):
+        lv = np.array([lat[k] for k in range(len(lat)) if infos[k][2] == v])
+        if len(lv):
+            per_vol["x".join(map(str, dims))] = {"n": int(len(lv)), "p50_s": round(float(np.percentile(lv, 50)), 3),
+                                                 "p99_s": round(float(np.percentile(lv, 99)), 3)}
+    print(json.dumps({"serve": f"{n} Poisson requests at 200/s, 4 volumes, 8 resident gauge fields, budget 80 GB",
+                      "inner": args.inner, "requests": n, "converged_to_tol": ok, "makespan_s": round(makespan, 3),
+                      "solves_per_s": round(n / makespan, 3),
+                      "latency_p50_s": round(float(np.percentile(lat_a, 50)), 3),
+                      "latency_p99_s": round(float(np.percentile(lat_a, 99)), 3), "per_volume": per_vol,
+                      "setup_s": round(setup_s, 1), "max_slots": args.serve_slots, "iters_per_step": args.serve_iters,
+                      "clocks": clk.summary()}))
+    srv.close()
     return 0
 
 
@@ -389,10 +540,23 @@ def main():
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--sweep-dims", default="64,64,64,128")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--recon", type=int, default=18, choices=[12, 18],
+                    help="reals stored per FP64 link (lower precisions always store 12)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the solver loop from the host (profiling: ncu lists every kernel)")
     ap.add_argument("--cpu-iters", type=int, default=20)
     ap.add_argument("--dslash-only", default=None, choices=["f64", "f32", "q16", "h16n", "b16n"],
                     help="time only the dslash of one precision on --sweep-dims (profiling case)")
+    ap.add_argument("--batch", action="store_true", help="batched 48-system multi-RHS solve (32^3x64)")
+    ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-iters", type=int, default=8)
     args = ap.parse_args()
+    if args.batch:
+        return run_batch(args)
+    if args.serve:
+        return run_serve(args)
     if args.dslash_only:
         return run_dslash_only(args)
     if args.impl == "reference":

@@ -167,6 +167,89 @@ wd_status wd_solve(wd_ctx *ctx, double *x, const double *b, double kappa, const 
 wd_status wd_solve_device(wd_ctx *ctx, void *x, const void *b, double kappa, const wd_solve_params *params,
                           wd_solve_info *info);
 
+/* Multi-right-hand-side dslash: out_r = D_{p,1-p} in_r (dagger: D^dag) for
+ * r = 0..nrhs-1, 1 <= nrhs <= 256.  in and out each hold nrhs single-parity
+ * fields of precision prec back to back (field r at byte offset
+ * r * wd_field_bytes(ctx, prec)).  One launch: every link is read from device
+ * memory once and applied to all right-hand sides (Sec. 3: one matrix, many
+ * source vectors).  The launch shape is the one the autotuner chose for the
+ * last batched solve of this nrhs and precision, else a default. */
+wd_status wd_dslash_batch(wd_ctx *ctx, void *out, const void *in, int nrhs, wd_parity out_parity, int dagger,
+                          wd_prec prec);
+
+/* Solve M_kappa_r x_r = b_r for n systems sharing the loaded gauge field
+ * (1 <= n <= 256), each with its own kappas[r] (host array): the 12
+ * spin-colour sources of a propagator times several masses.  Even-odd Schur
+ * BiCGstab with the reliable-update mixed precision of Alg. 2 (Sec. 5), all
+ * systems in lockstep in one CUDA graph; converged systems stop doing work;
+ * reliable updates are batched over the systems that need one.
+ * params->solver must be WD_BICGSTAB.  The multi-RHS dslash shape (RHS tile
+ * and grid) is chosen by timing on the first call for (lattice, precision,
+ * n), and cached in the context and, when the environment variable
+ * WD_TUNE_CACHE names a file, in that file.  infos[r] is filled for every
+ * system; the return value is WD_OK when all converged, else the first
+ * failing status.
+ * wd_solve_batch_device: x and b are n FP64 full fields (even then odd, the
+ *   internal layout) back to back, system r at byte offset
+ *   r * 2 * wd_field_bytes(ctx, WD_F64).
+ * wd_solve_batch: x[r], b[r] are host FP64 fields in the host layout. */
+wd_status wd_solve_batch_device(wd_ctx *ctx, int n, void *x, const void *b, const double *kappas,
+                                const wd_solve_params *params, wd_solve_info *infos);
+wd_status wd_solve_batch(wd_ctx *ctx, int n, double *const *x, const double *const *b, const double *kappas,
+                         const wd_solve_params *params, wd_solve_info *infos);
+
+/* ---- Serving: continuous batching of solve requests ----------------------
+ * A server keeps several gauge fields resident (possibly of different
+ * lattice volumes), queues solve requests against them and runs them as
+ * slots of batched, lockstep reliable-update BiCGstab solves (Sec. 5 and the
+ * batched solver above).  Requests that arrive while others are running are
+ * admitted at the next step as slots and memory free up; every device
+ * allocation is charged against budget_bytes.  Each gauge field has its own
+ * CUDA stream, so solves on different volumes overlap on the device.  A
+ * request's iterates follow the same kernel sequence alone and in a mix. */
+typedef struct wd_server wd_server;
+
+typedef struct {
+  size_t budget_bytes; /* device memory for gauge fields and solver slots; 0 = no limit */
+  int max_slots;       /* concurrent solves per gauge field, 1..256                   */
+  int iters_per_step;  /* lockstep iterations per wd_server_step between admissions   */
+  int inner_precision; /* wd_prec of the inner iteration                              */
+  double delta;        /* reliable-update threshold (Alg. 2)                          */
+  int max_iter;        /* per request                                                 */
+  int use_graph;       /* 1: each step's iterations run as one CUDA graph             */
+} wd_server_params;
+
+wd_status wd_server_create(wd_server **out, const wd_server_params *params);
+wd_status wd_server_destroy(wd_server *server);
+
+/* Make a gauge field resident (host layout, FP64; recon 12 or 18 as in
+ * wd_load_gauge).  Its copies, staging and scratch are charged against the
+ * budget (WD_ERR_BUDGET if they do not fit).  *gauge_id names it in requests. */
+wd_status wd_server_add_gauge(wd_server *server, const int dims[4], int t_antiperiodic, const double *U, int recon,
+                              int *gauge_id);
+
+/* Queue M_kappa x = b to |b - M x| <= tol |b| on gauge field gauge_id.  b and
+ * x are host FP64 fields in the host layout that the caller keeps alive until
+ * the request has finished; x is written when it finishes.  WD_ERR_BUDGET if
+ * even one slot for this lattice can never fit the budget. */
+wd_status wd_server_submit(wd_server *server, int gauge_id, const double *b, double *x, double kappa, double tol,
+                           long long *request_id);
+
+/* One scheduling round: retire the requests that finished during the previous
+ * round (reconstruction, FP64 true residual, x copied out), release the slot
+ * memory of idle gauge fields, admit queued requests into free slots within the
+ * budget, then run up to iters_per_step lockstep iterations on every gauge field
+ * with active slots (concurrently, one stream each) and wait for them.
+ * *active / *queued receive the numbers of running and waiting requests. */
+wd_status wd_server_step(wd_server *server, int *active, int *queued);
+
+/* *finished = 1 and *info filled once the request has been retired. */
+wd_status wd_server_poll(wd_server *server, long long request_id, int *finished, wd_solve_info *info);
+
+/* Device bytes currently charged against the budget. */
+size_t wd_server_memory_in_use(const wd_server *server);
+const char *wd_server_last_error(const wd_server *server);
+
 /* |field|^2 of one single-parity device field, in FP64, for callers that
  * cannot allocate device memory.  (The paper has no counterpart; this is a
  * service of the library.)  Such callers -- code whose host framework owns all

@@ -50,6 +50,12 @@ class SolveInfo(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong)]
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("iters_per_step", ctypes.c_int),
+                ("inner_precision", ctypes.c_int), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -81,6 +87,19 @@ def load_library():
         "wd_norm2": (c_int, [vp, dp, vp, c_int]),
         "wd_solve": (c_int, [vp, vp, vp, c_dbl, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "wd_solve_device": (c_int, [vp, vp, vp, c_dbl, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "wd_dslash_batch": (c_int, [vp, vp, vp, c_int, c_int, c_int, c_int]),
+        "wd_solve_batch_device": (c_int, [vp, c_int, vp, vp, dp, ctypes.POINTER(SolveParams),
+                                          ctypes.POINTER(SolveInfo)]),
+        "wd_solve_batch": (c_int, [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), dp,
+                                   ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "wd_server_create": (c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerParams)]),
+        "wd_server_destroy": (c_int, [vp]),
+        "wd_server_add_gauge": (c_int, [vp, ip, c_int, vp, c_int, ip]),
+        "wd_server_submit": (c_int, [vp, c_int, vp, vp, c_dbl, c_dbl, ctypes.POINTER(ctypes.c_longlong)]),
+        "wd_server_step": (c_int, [vp, ip, ip]),
+        "wd_server_poll": (c_int, [vp, ctypes.c_longlong, ip, ctypes.POINTER(SolveInfo)]),
+        "wd_server_memory_in_use": (ctypes.c_size_t, [vp]),
+        "wd_server_last_error": (ctypes.c_char_p, [vp]),
         "wd_last_error": (ctypes.c_char_p, [vp]),
         "wd_status_string": (ctypes.c_char_p, [c_int]),
     }
@@ -96,7 +115,10 @@ def exported_symbols():
     lib = load_library()
     return [n for n in ("wd_create", "wd_destroy", "wd_set_stream", "wd_field_bytes", "wd_load_gauge",
                         "wd_field_import", "wd_field_export", "wd_dslash", "wd_dslash_xpay", "wd_apply_M", "wd_norm2",
-                        "wd_solve", "wd_solve_device", "wd_norm2_noalloc", "wd_last_error", "wd_status_string")
+                        "wd_solve", "wd_solve_device", "wd_dslash_batch", "wd_solve_batch", "wd_solve_batch_device",
+                        "wd_server_create", "wd_server_destroy", "wd_server_add_gauge", "wd_server_submit",
+                        "wd_server_step", "wd_server_poll", "wd_server_memory_in_use", "wd_server_last_error",
+                        "wd_norm2_noalloc", "wd_last_error", "wd_status_string")
             if hasattr(lib, n)]
 
 
@@ -233,6 +255,44 @@ class WilsonDirac:
         return self._solve(self.lib.wd_solve_device, x, b, kappa, tol, delta, max_iter, solver, inner_precision,
                            use_graph, check)
 
+    def dslash_batch(self, out, inp, nrhs: int, out_parity: int, dagger: bool, prec: int):
+        """out_r = D in_r for nrhs single-parity fields stored back to back."""
+        self._check(self.lib.wd_dslash_batch(self.ctx, _ptr(out), _ptr(inp), int(nrhs), out_parity, int(dagger), prec),
+                    "dslash_batch")
+
+    @staticmethod
+    def _infos(arr, n):
+        return [SolveResult(int(i.status), int(i.iters), int(i.reliable_updates), float(i.true_rel_residual),
+                            float(i.iterated_rel_residual), float(i.seconds), int(i.kernel_launches))
+                for i in arr[:n]]
+
+    def solve_batch_device(self, x, b, kappas, tol=1e-12, delta=0.1, max_iter=20000, inner_precision=Q16,
+                           use_graph=True, check=True):
+        """x, b: n FP64 full fields back to back (``new_field(F64, 2 * n)``)."""
+        n = len(kappas)
+        k = (ctypes.c_double * n)(*[float(v) for v in kappas])
+        p = self._params(tol, delta, max_iter, BICGSTAB, inner_precision, use_graph)
+        infos = (SolveInfo * n)()
+        st = self.lib.wd_solve_batch_device(self.ctx, n, _ptr(x), _ptr(b), k, ctypes.byref(p), infos)
+        if st not in (0, 4, 5, 6) or (check and st != 0):
+            self._check(st, "solve_batch_device")
+        return self._infos(infos, n)
+
+    def solve_batch(self, xs, bs, kappas, tol=1e-12, delta=0.1, max_iter=20000, inner_precision=Q16,
+                    use_graph=True, check=True):
+        """xs, bs: lists of (V, 4, 3) complex128 host arrays."""
+        n = len(kappas)
+        bs = [np.ascontiguousarray(b, dtype=np.complex128) for b in bs]
+        xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+        bp = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+        k = (ctypes.c_double * n)(*[float(v) for v in kappas])
+        p = self._params(tol, delta, max_iter, BICGSTAB, inner_precision, use_graph)
+        infos = (SolveInfo * n)()
+        st = self.lib.wd_solve_batch(self.ctx, n, xp, bp, k, ctypes.byref(p), infos)
+        if st not in (0, 4, 5, 6) or (check and st != 0):
+            self._check(st, "solve_batch")
+        return self._infos(infos, n)
+
     # -- conveniences built only from the calls above
     def upload(self, lex, prec: int, parity: int | None = None):
         """Host (V,4,3) complex128 -> device field (one parity, or both when parity is None)."""
@@ -257,3 +317,77 @@ class WilsonDirac:
         else:
             self.field_export(out, field, parity, prec)
         return out
+
+
+class Server:
+    """Continuous-batching solve server (``wd_server_*``): resident gauge
+    fields, a device-memory budget, requests admitted as slots free up."""
+
+    def __init__(self, budget_bytes=0, max_slots=8, iters_per_step=8, inner_precision=Q16, delta=0.1,
+                 max_iter=20000, use_graph=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the Wilson-Dirac library runs on the GPU only")
+        self.lib = load_library()
+        p = ServerParams(int(budget_bytes), int(max_slots), int(iters_per_step), int(inner_precision), float(delta),
+                         int(max_iter), int(use_graph))
+        h = ctypes.c_void_p()
+        st = self.lib.wd_server_create(ctypes.byref(h), ctypes.byref(p))
+        if st != 0:
+            raise WDError(st, "wd_server_create failed")
+        self.h = h
+        self._keep = {}  # request id -> (b, x) host arrays kept alive until retired
+
+    def _check(self, st, what):
+        if st != 0:
+            raise WDError(st, f"{what}: {self.lib.wd_server_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.wd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_gauge(self, dims, U, recon=12, t_antiperiodic=False) -> int:
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+        gid = ctypes.c_int()
+        self._check(self.lib.wd_server_add_gauge(self.h, d, int(bool(t_antiperiodic)), _ptr(U), int(recon),
+                                                 ctypes.byref(gid)), "add_gauge")
+        return gid.value
+
+    def submit(self, gauge_id, b, kappa, tol, x=None) -> int:
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        if x is None:
+            x = np.zeros_like(b)
+        rid = ctypes.c_longlong()
+        self._check(self.lib.wd_server_submit(self.h, int(gauge_id), _ptr(b), _ptr(x), float(kappa), float(tol),
+                                              ctypes.byref(rid)), "submit")
+        self._keep[rid.value] = (b, x)
+        return rid.value
+
+    def step(self):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wd_server_step(self.h, ctypes.byref(a), ctypes.byref(q)), "step")
+        return a.value, q.value
+
+    def poll(self, rid):
+        """(finished, SolveResult or None, x or None)"""
+        f = ctypes.c_int()
+        info = SolveInfo()
+        self._check(self.lib.wd_server_poll(self.h, int(rid), ctypes.byref(f), ctypes.byref(info)), "poll")
+        if not f.value:
+            return False, None, None
+        b, x = self._keep.pop(rid, (None, None))
+        res = SolveResult(int(info.status), int(info.iters), int(info.reliable_updates),
+                          float(info.true_rel_residual), float(info.iterated_rel_residual), float(info.seconds),
+                          int(info.kernel_launches))
+        return True, res, x
+
+    def memory_in_use(self) -> int:
+        return int(self.lib.wd_server_memory_in_use(self.h))

@@ -16,7 +16,11 @@
 #include <string>
 #include <vector>
 
-#include "wd_kernels.cuh"
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+
+#include "wd_batch.cuh"
 
 namespace wd {
 
@@ -109,6 +113,66 @@ __global__ void gauge_f64_to_16_kernel(Geom g, const double2* in, int nc, uint4*
   }
 }
 
+// Batch loop control, last node of the batched WHILE body: continue while a
+// system is unconverged; bounded on its own at max_iter + 16 executions.
+__global__ void batch_loop_control_kernel(BatchCtl* bc, const SolverCtl* ctl_in, int nrhs) {
+  SolverCtl* ctl = const_cast<SolverCtl*>(ctl_in);
+  int all = 1;
+  for (int r = 0; r < nrhs; ++r)
+    if (!ctl[r].done) all = 0;
+  bc->loops += 1;
+  bc->step_loops += 1;
+  if (!all && bc->loops > bc->max_loops) {
+    for (int r = 0; r < nrhs; ++r)
+      if (!ctl[r].done) {
+        ctl[r].done = 1;
+        if (ctl[r].status == WD_OK) ctl[r].status = WD_ERR_NOT_CONVERGED;
+      }
+    all = 1;
+  }
+  bc->all_done = all;
+  const int cont = !all && bc->step_loops < bc->step_limit;
+  if (bc->in_graph) cudaGraphSetConditional((cudaGraphConditionalHandle)bc->h_loop, cont ? 1u : 0u);
+}
+
+__global__ void batch_init_kernel(SolverCtl* ctl, BatchCtl* bc, int nrhs, double tol, double delta, int max_iter,
+                                  const double* kappas, const double* bnorm2, int in_graph,
+                                  unsigned long long h_update, unsigned long long h_loop) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrhs) {
+    SolverCtl c;
+    memset(&c, 0, sizeof(c));
+    c.rho = c.rho_prev = c.alpha = c.omega = make_double2(1.0, 0.0);
+    c.beta = make_double2(0.0, 0.0);
+    const double b2 = bnorm2[r] + bnorm2[nrhs + r];
+    c.stop2 = tol * tol * b2;
+    c.delta = delta;
+    c.kappa = kappas[r];
+    c.neg_kappa2 = -kappas[r] * kappas[r];
+    c.max_iter = max_iter;
+    c.status = WD_OK;
+    if (!isfinite(b2)) {
+      c.status = WD_ERR_NUMERIC;
+      c.done = 1;
+    } else if (b2 == 0.0) {
+      c.done = 1;  // zero source: x = 0
+    }
+    ctl[r] = c;
+  }
+  if (r == 0) {
+    for (int k = 0; k < 4; ++k) bc->counter[k] = 0;
+    bc->any_update = 0;
+    bc->all_done = 0;
+    bc->in_graph = in_graph;
+    bc->loops = 0;
+    bc->max_loops = max_iter + 16;
+    bc->step_loops = 0;
+    bc->step_limit = max_iter + 16;
+    bc->h_update = h_update;
+    bc->h_loop = h_loop;
+  }
+}
+
 const PrecOps* prec_ops(int p) {
   switch (p) {
     case WD_F64: return ops_f64();
@@ -123,10 +187,6 @@ const PrecOps* prec_ops(int p) {
 }  // namespace wd
 
 using namespace wd;
-
-struct wd_ctx {
-  Ctx c;
-};
 
 namespace {
 
@@ -464,6 +524,25 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
 
 }  // namespace
 
+wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, const void* odd) {
+  Ctx& c = ctx->c;
+  wd_status st = ensure_staging(ctx);
+  if (st != WD_OK) return st;
+  const PrecOps* o = ops_f64();
+  o->export_lex(c, c.lex_staging, even, 0, c.stream);
+  o->export_lex(c, c.lex_staging, odd, 1, c.stream);
+  WD_CK_LAUNCH(ctx, "export");
+  WD_CK(ctx, cudaMemcpyAsync(host, c.lex_staging, (size_t)2 * c.g.Vh * 24 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c.stream));
+  WD_CK(ctx, cudaStreamSynchronize(c.stream));
+  return WD_OK;
+}
+
+wd_status wd_internal_ensure_gauge(wd_ctx* ctx, int prec) {
+  if (!ctx || prec < WD_F64 || prec > WD_B16N) return WD_ERR_INVALID_ARG;
+  return ensure_gauge(ctx, prec);
+}
+
 extern "C" {
 
 const char* wd_status_string(wd_status s) {
@@ -496,14 +575,7 @@ wd_status wd_create(wd_ctx** out, const int dims[4], int t_antiperiodic, void* c
   wd_ctx* ctx = new (std::nothrow) wd_ctx();
   if (!ctx) return WD_ERR_OOM;
   Ctx& c = ctx->c;
-  c.g.X = dims[0];
-  c.g.Y = dims[1];
-  c.g.Z = dims[2];
-  c.g.T = dims[3];
-  c.g.Xh = dims[0] / 2;
-  c.g.Vh = (int)(v / 2);
-  c.g.stride = round_up(c.g.Vh, 32);
-  c.g.tbc_anti = t_antiperiodic ? 1 : 0;
+  c.g = make_geom(dims, t_antiperiodic);
   memcpy(c.dims, dims, sizeof(c.dims));
   c.stream = (cudaStream_t)cuda_stream;
   c.recon = 12;
@@ -551,6 +623,7 @@ wd_status wd_destroy(wd_ctx* ctx) {
   dev_free((void*&)c.sb.ctl);
   dev_free(c.sb_full[0]);
   dev_free(c.sb_full[1]);
+  batch_release(c);
   if (c.host_pinned) cudaFreeHost(c.host_pinned);
   delete ctx;
   return WD_OK;

@@ -14,22 +14,69 @@
 namespace wd {
 
 // ------------------------------------------------------------------ geometry
+// Division of n < 2^31 by a fixed d with one multiply-high and a shift
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  uint32_t m;
+  int s;
+};
+
+inline FastDiv make_fastdiv(int d) {
+  int s = 0;
+  while ((1LL << s) < d) ++s;
+  const unsigned long long m = ((1ULL << 32) * ((1ULL << s) - (unsigned long long)d)) / (unsigned long long)d + 1;
+  return FastDiv{(uint32_t)m, s};
+}
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return (int)((__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.s);
+}
+
 struct Geom {
   int X, Y, Z, T;
   int Xh;      // X / 2
   int Vh;      // sites of one parity
   int stride;  // elements between component arrays of a field (>= Vh)
   int tbc_anti;
+  int XhY, XhYZ;      // even-odd index steps in y, z (t step is XhYZ)
+  int wy, wz, wt;     // index jumps of the periodic wrap in y, z, t
+  FastDiv dXh, dY, dZ;
 };
 
+inline Geom make_geom(const int dims[4], int tbc_anti) {
+  Geom g{};
+  g.X = dims[0];
+  g.Y = dims[1];
+  g.Z = dims[2];
+  g.T = dims[3];
+  g.Xh = dims[0] / 2;
+  const long long vh = (long long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
+  g.Vh = (int)vh;
+  g.stride = (int)((vh + 31) / 32 * 32);
+  g.tbc_anti = tbc_anti ? 1 : 0;
+  g.XhY = g.Xh * g.Y;
+  g.XhYZ = g.XhY * g.Z;
+  g.wy = (g.Y - 1) * g.Xh;
+  g.wz = (g.Z - 1) * g.XhY;
+  g.wt = (g.T - 1) * g.XhYZ;
+  g.dXh = make_fastdiv(g.Xh);
+  g.dY = make_fastdiv(g.Y);
+  g.dZ = make_fastdiv(g.Z);
+  return g;
+}
+
 __device__ __forceinline__ void site_coords(const Geom& g, int h, int parity, int& x, int& y, int& z, int& t) {
-  int r = h;
-  int xh = r % g.Xh;
-  r /= g.Xh;
-  y = r % g.Y;
-  r /= g.Y;
-  z = r % g.Z;
-  t = r / g.Z;
+  int q = fdiv(h, g.dXh);
+  const int xh = h - q * g.Xh;
+  int r = q;
+  q = fdiv(r, g.dY);
+  y = r - q * g.Y;
+  r = q;
+  q = fdiv(r, g.dZ);
+  z = r - q * g.Z;
+  t = q;
   x = 2 * xh + ((y + z + t + parity) & 1);
 }
 
@@ -48,9 +95,16 @@ constexpr float kInv32767 = 3.0518509475997192e-05f;  // (float)(1.0 / 32767.0)
 
 struct SpinorF64 {
   using real = double;
+  static constexpr bool kScaled = false;
   double2* p;
   int stride;
+  size_t rs;  // bytes from one right-hand side's field to the next (batches)
   static constexpr int kBytesPerSite = 192;
+  __device__ __forceinline__ SpinorF64 at(int r) const {
+    SpinorF64 v = *this;
+    v.p = (double2*)((char*)p + (size_t)r * rs);
+    return v;
+  }
   template <typename R>
   __device__ __forceinline__ void load(int h, R (&v)[24]) const {
 #pragma unroll
@@ -74,9 +128,16 @@ struct SpinorF64 {
 
 struct SpinorF32 {
   using real = float;
+  static constexpr bool kScaled = false;
   float4* p;
   int stride;
+  size_t rs;
   static constexpr int kBytesPerSite = 96;
+  __device__ __forceinline__ SpinorF32 at(int r) const {
+    SpinorF32 v = *this;
+    v.p = (float4*)((char*)p + (size_t)r * rs);
+    return v;
+  }
   template <typename R>
   __device__ __forceinline__ void load(int h, R (&v)[24]) const {
 #pragma unroll
@@ -120,20 +181,43 @@ enum class Fmt16 { Q16, H16, B16 };
 template <Fmt16 F>
 struct Spinor16 {
   using real = float;
+  static constexpr bool kScaled = true;  // load_raw + one scale per site
   uint4* p;      // [3][stride]
   float* norm;   // [stride]
   int stride;
+  size_t rs;
   static constexpr int kBytesPerSite = 52;
+  __device__ __forceinline__ Spinor16 at(int r) const {
+    Spinor16 v = *this;
+    v.p = (uint4*)((char*)p + (size_t)r * rs);
+    v.norm = (float*)((char*)norm + (size_t)r * rs);
+    return v;
+  }
 
+  // int16 code q -> float q exactly, on the integer and FP32 pipes: the
+  // offset-binary value q + 32768 is placed in the mantissa of 2^23 and the
+  // sum 2^23 + 2^15 subtracted (no int-to-float conversion instruction).
+  static __device__ __forceinline__ float q16_to_float(uint32_t half_bits) {
+    return __uint_as_float(0x4B000000u | (half_bits ^ 0x8000u)) - 8421376.0f;
+  }
   static __device__ __forceinline__ float lo(uint32_t w) {
-    if constexpr (F == Fmt16::Q16) return (float)(int16_t)(w & 0xffffu);
+    if constexpr (F == Fmt16::Q16) return q16_to_float(w & 0xffffu);
     else if constexpr (F == Fmt16::H16) return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
     else return __uint_as_float(w << 16);
   }
   static __device__ __forceinline__ float hi(uint32_t w) {
-    if constexpr (F == Fmt16::Q16) return (float)(int16_t)(w >> 16);
+    if constexpr (F == Fmt16::Q16) return q16_to_float(w >> 16);
     else if constexpr (F == Fmt16::H16) return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
     else return __uint_as_float(w & 0xffff0000u);
+  }
+  // both values of a 32-bit word
+  static __device__ __forceinline__ float2 pair(uint32_t w) {
+    if constexpr (F == Fmt16::H16) {
+      __half2 h = *reinterpret_cast<__half2*>(&w);
+      return __half22float2(h);
+    } else {
+      return make_float2(lo(w), hi(w));
+    }
   }
   // raw 16-bit values as float (codes, or the normalised fp16/bf16 numbers)
   // plus the factor that turns them into field values
@@ -141,10 +225,13 @@ struct Spinor16 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       uint4 d = __ldg(p + (size_t)c * stride + h);
-      v[8 * c + 0] = lo(d.x); v[8 * c + 1] = hi(d.x);
-      v[8 * c + 2] = lo(d.y); v[8 * c + 3] = hi(d.y);
-      v[8 * c + 4] = lo(d.z); v[8 * c + 5] = hi(d.z);
-      v[8 * c + 6] = lo(d.w); v[8 * c + 7] = hi(d.w);
+      const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = pair(w[j]);
+        v[8 * c + 2 * j] = f.x;
+        v[8 * c + 2 * j + 1] = f.y;
+      }
     }
     float n = __ldg(norm + h);
     if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
@@ -234,6 +321,8 @@ __device__ __forceinline__ void reconstruct_row3(R (&u)[18]) {
 
 struct GaugeF64 {
   using real = double;
+  static constexpr bool kScaled = false;
+  static constexpr double kScale = 1.0;
   const double2* p;
   int stride;
   int recon;  // 12 or 18
@@ -261,6 +350,8 @@ struct GaugeF64 {
 
 struct GaugeF32 {
   using real = float;
+  static constexpr bool kScaled = false;
+  static constexpr float kScale = 1.f;
   const float4* p;
   int stride;
   __device__ __forceinline__ void load(int parity, int mu, int h, float (&u)[18]) const {
@@ -280,21 +371,37 @@ struct GaugeF32 {
 template <Fmt16 F>
 struct Gauge16 {
   using real = float;
+  // Q16 links are used as raw codes: load_raw returns 32767 U (row c rebuilt
+  // from the raw rows and rescaled), and kScale = 1/32767 is folded into the
+  // accumulation.  fp16 / bf16 links hold U itself.
+  static constexpr bool kScaled = (F == Fmt16::Q16);
+  static constexpr float kScale = kInv32767;
   const uint4* p8;  // [p][mu][stride]: reals 0..7
   const uint2* p4;  // [p][mu][stride]: reals 8..11
   int stride;
-  __device__ __forceinline__ void load(int parity, int mu, int h, float (&u)[18]) const {
+  __device__ __forceinline__ void load_raw(int parity, int mu, int h, float (&u)[18]) const {
     size_t o = (size_t)(parity * 4 + mu) * stride + h;
     uint4 a = __ldcs(p8 + o);
     uint2 b = __ldcs(p4 + o);
     uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
-    const float s = (F == Fmt16::Q16) ? kInv32767 : 1.f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      u[2 * k] = Spinor16<F>::lo(w[k]) * s;
-      u[2 * k + 1] = Spinor16<F>::hi(w[k]) * s;
+      const float2 f = Spinor16<F>::pair(w[k]);
+      u[2 * k] = f.x;
+      u[2 * k + 1] = f.y;
     }
     reconstruct_row3(u);
+    if constexpr (F == Fmt16::Q16) {
+#pragma unroll
+      for (int k = 12; k < 18; ++k) u[k] *= kInv32767;
+    }
+  }
+  __device__ __forceinline__ void load(int parity, int mu, int h, float (&u)[18]) const {
+    load_raw(parity, mu, h, u);
+    if constexpr (F == Fmt16::Q16) {
+#pragma unroll
+      for (int k = 0; k < 18; ++k) u[k] *= kInv32767;
+    }
   }
 };
 
@@ -364,6 +471,33 @@ __device__ __forceinline__ void reconstruct(const R (&g)[12], R (&a)[24]) {
   }
 }
 
+// reconstruct() with every term scaled by w (the decode scale of a 16-bit
+// neighbour and link, times a boundary sign): a += w P psi' in one FFMA each
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct_scaled(const R (&g)[12], R (&a)[24], R w) {
+  const R ws = w * (R)S;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R g0r = g[c * 2], g0i = g[c * 2 + 1];
+    const R g1r = g[(3 + c) * 2], g1i = g[(3 + c) * 2 + 1];
+    a[(0 + c) * 2] += w * g0r; a[(0 + c) * 2 + 1] += w * g0i;
+    a[(3 + c) * 2] += w * g1r; a[(3 + c) * 2 + 1] += w * g1i;
+    if constexpr (MU == 0) {
+      a[(6 + c) * 2] += ws * g1i; a[(6 + c) * 2 + 1] -= ws * g1r;
+      a[(9 + c) * 2] += ws * g0i; a[(9 + c) * 2 + 1] -= ws * g0r;
+    } else if constexpr (MU == 1) {
+      a[(6 + c) * 2] += ws * g1r; a[(6 + c) * 2 + 1] += ws * g1i;
+      a[(9 + c) * 2] -= ws * g0r; a[(9 + c) * 2 + 1] -= ws * g0i;
+    } else if constexpr (MU == 2) {
+      a[(6 + c) * 2] += ws * g0i; a[(6 + c) * 2 + 1] -= ws * g0r;
+      a[(9 + c) * 2] -= ws * g1i; a[(9 + c) * 2 + 1] += ws * g1r;
+    } else {
+      a[(6 + c) * 2] += ws * g0r; a[(6 + c) * 2 + 1] += ws * g0i;
+      a[(9 + c) * 2] += ws * g1r; a[(9 + c) * 2 + 1] += ws * g1i;
+    }
+  }
+}
+
 // g = U h (DAG = false) or U^dag h (DAG = true), for both spin rows of h
 template <bool DAG, typename R>
 __device__ __forceinline__ void su3_mul(const R (&u)[18], const R (&h)[12], R (&g)[12]) {
@@ -392,22 +526,37 @@ template <int MU, bool FWD, bool DAGGER, typename R, class In, class G>
 __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, int h_link, int h_nbr, bool flip,
                                     R (&acc)[24]) {
   constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  constexpr bool kScaled = In::kScaled || G::kScaled;
   R psi[24];
-  in.load(h_nbr, psi);
+  R w = 1;
+  if constexpr (In::kScaled) w = in.load_raw(h_nbr, psi);
+  else in.load(h_nbr, psi);
   R hs[12];
   project<MU, S>(psi, hs);
   R u[18];
-  gauge.load(FWD ? parity : 1 - parity, MU, h_link, u);
+  if constexpr (G::kScaled) {
+    gauge.load_raw(FWD ? parity : 1 - parity, MU, h_link, u);
+    w *= (R)G::kScale;
+  } else {
+    gauge.load(FWD ? parity : 1 - parity, MU, h_link, u);
+  }
   R gs[12];
   su3_mul<!FWD>(u, hs, gs);
-  if (flip) {
+  if constexpr (kScaled) {
+    reconstruct_scaled<MU, S>(gs, acc, flip ? -w : w);
+  } else {
+    if (flip) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) gs[k] = -gs[k];
+      for (int k = 0; k < 12; ++k) gs[k] = -gs[k];
+    }
+    reconstruct<MU, S>(gs, acc);
   }
-  reconstruct<MU, S>(gs, acc);
 }
 
-// acc = (D in)(site h of parity `parity`), or (D^dag in)(h)
+// acc = (D in)(site h of parity `parity`), or (D^dag in)(h).  Neighbour
+// indices by offsets from h: in the even-odd order a step in y, z, t moves
+// the index by X/2, XY/2, XYZ/2; a step in x moves it by 0 or 1 depending on
+// the parity of x.
 template <bool DAGGER, typename R, class In, class G>
 __device__ __forceinline__ void dslash_site(const Geom& g, const In& in, const G& gauge, int h, int parity,
                                             R (&acc)[24]) {
@@ -416,29 +565,30 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const In& in, const G
 #pragma unroll
   for (int k = 0; k < 24; ++k) acc[k] = 0;
   {
-    const int xp = (x + 1 == g.X) ? 0 : x + 1, xm = (x == 0) ? g.X - 1 : x - 1;
-    hop<0, true, DAGGER>(in, gauge, parity, h, cb_index(g, xp, y, z, t), false, acc);
-    const int n = cb_index(g, xm, y, z, t);
-    hop<0, false, DAGGER>(in, gauge, parity, n, n, false, acc);
+    const int xo = x & 1;
+    const int np = (x == g.X - 1) ? h - (g.Xh - 1) : h + xo;
+    const int nm = (x == 0) ? h + (g.Xh - 1) : h - (xo ^ 1);
+    hop<0, true, DAGGER>(in, gauge, parity, h, np, false, acc);
+    hop<0, false, DAGGER>(in, gauge, parity, nm, nm, false, acc);
   }
   {
-    const int yp = (y + 1 == g.Y) ? 0 : y + 1, ym = (y == 0) ? g.Y - 1 : y - 1;
-    hop<1, true, DAGGER>(in, gauge, parity, h, cb_index(g, x, yp, z, t), false, acc);
-    const int n = cb_index(g, x, ym, z, t);
-    hop<1, false, DAGGER>(in, gauge, parity, n, n, false, acc);
+    const int np = (y == g.Y - 1) ? h - g.wy : h + g.Xh;
+    const int nm = (y == 0) ? h + g.wy : h - g.Xh;
+    hop<1, true, DAGGER>(in, gauge, parity, h, np, false, acc);
+    hop<1, false, DAGGER>(in, gauge, parity, nm, nm, false, acc);
   }
   {
-    const int zp = (z + 1 == g.Z) ? 0 : z + 1, zm = (z == 0) ? g.Z - 1 : z - 1;
-    hop<2, true, DAGGER>(in, gauge, parity, h, cb_index(g, x, y, zp, t), false, acc);
-    const int n = cb_index(g, x, y, zm, t);
-    hop<2, false, DAGGER>(in, gauge, parity, n, n, false, acc);
+    const int np = (z == g.Z - 1) ? h - g.wz : h + g.XhY;
+    const int nm = (z == 0) ? h + g.wz : h - g.XhY;
+    hop<2, true, DAGGER>(in, gauge, parity, h, np, false, acc);
+    hop<2, false, DAGGER>(in, gauge, parity, nm, nm, false, acc);
   }
   {
-    const bool top = (t + 1 == g.T), bot = (t == 0);
-    const int tp = top ? 0 : t + 1, tm = bot ? g.T - 1 : t - 1;
-    hop<3, true, DAGGER>(in, gauge, parity, h, cb_index(g, x, y, z, tp), top && g.tbc_anti, acc);
-    const int n = cb_index(g, x, y, z, tm);
-    hop<3, false, DAGGER>(in, gauge, parity, n, n, bot && g.tbc_anti, acc);
+    const bool top = (t == g.T - 1), bot = (t == 0);
+    const int np = top ? h - g.wt : h + g.XhYZ;
+    const int nm = bot ? h + g.wt : h - g.XhYZ;
+    hop<3, true, DAGGER>(in, gauge, parity, h, np, top && g.tbc_anti, acc);
+    hop<3, false, DAGGER>(in, gauge, parity, nm, nm, bot && g.tbc_anti, acc);
   }
 }
 

@@ -42,6 +42,8 @@ struct SolverCtl {
 };
 
 struct Ctx;
+struct BatchLaunch;
+struct BatchBufs;
 
 // Per-precision operations, one table per storage precision.
 struct PrecOps {
@@ -67,8 +69,12 @@ struct PrecOps {
   void (*cg_iteration)(const Ctx&, struct SolveBufs&, cudaStream_t);
   void (*cg_update)(const Ctx&, struct SolveBufs&, cudaStream_t);
   void (*cg_setup)(const Ctx&, struct SolveBufs&, cudaStream_t);
-  // derive this precision's gauge copy from the FP64 copy
-  void (*gauge_from_f64)(Ctx&, cudaStream_t);
+  // S11: multi-RHS dslash and the batched BiCGstab with this inner precision
+  void (*dslash_batch)(const Ctx&, const BatchLaunch&, void* out, const void* in, int parity, int dagger,
+                       cudaStream_t);
+  void (*batch_setup)(const Ctx&, const BatchLaunch&, BatchBufs&, cudaStream_t);
+  void (*batch_iteration)(const Ctx&, const BatchLaunch&, BatchBufs&, cudaStream_t);
+  void (*batch_update)(const Ctx&, const BatchLaunch&, BatchBufs&, cudaStream_t);
 };
 
 const PrecOps* ops_f64();
@@ -126,11 +132,32 @@ struct Ctx {
   cudaGraph_t graph;
   int graph_prec, graph_solver;
   unsigned long long graph_hu, graph_hl;  // conditional handles of the graph
+  // batched solves (S11): workspace, graph and tuned launch shapes
+  void* batch_block;
+  size_t batch_bytes;
+  int batch_n, batch_prec;
+  void* batch_small;      // ctl array, BatchCtl, partials, kappas, scalars
+  cudaGraphExec_t batch_exec;
+  cudaGraph_t batch_graph;
+  unsigned long long batch_hu, batch_hl;
+  int batch_tr, batch_grid;  // tuned multi-RHS dslash shape for (batch_n, batch_prec)
+  double* batch_host;     // pinned mirror of per-system results
   std::string last_error;
 };
+
+void batch_release(Ctx& c);  // frees the batched-solve workspace (wd_solve_batch.cu)
 
 // helpers
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 }  // namespace wd
+
+struct wd_ctx {
+  wd::Ctx c;
+};
+
+// derive the gauge copy of precision prec from the FP64 copy if missing
+wd_status wd_internal_ensure_gauge(wd_ctx* ctx, int prec);
+// host FP64 field (host layout) <- two single-parity FP64 device fields
+wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, const void* odd);

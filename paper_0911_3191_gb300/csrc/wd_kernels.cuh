@@ -22,7 +22,9 @@ constexpr int kBlasBlock = 256;
 struct Coef {
   double c;
   const double* p;
+  long rs = 0;  // doubles from one right-hand side's value to the next
   __device__ __forceinline__ double get() const { return p ? *p : c; }
+  __device__ __forceinline__ Coef at(int r) const { return Coef{c, p ? p + (long)r * rs : nullptr, rs}; }
 };
 
 // ---------------------------------------------------------- finalisers
@@ -38,6 +40,7 @@ __device__ __forceinline__ void ctl_set_update(SolverCtl* ctl, int v) {
 struct FinStore {
   double* out;
   int n;
+  __device__ __forceinline__ FinStore at(int r) const { return FinStore{out + (long)r * n, n}; }
   __device__ void operator()(const double* t) const {
     for (int k = 0; k < n; ++k) out[k] = t[k];
   }
@@ -46,6 +49,7 @@ struct FinStore {
 // BiCGstab: alpha = rho / <r_tilde, v>
 struct FinBicgAlpha {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinBicgAlpha at(int r) const { return FinBicgAlpha{ctl + r}; }
   __device__ void operator()(const double* t) const {
     double2 rtv = make_double2(t[0], t[1]);
     if (!cfinite(rtv)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
@@ -57,6 +61,7 @@ struct FinBicgAlpha {
 // BiCGstab: omega = <t, s> / <t, t>
 struct FinBicgOmega {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinBicgOmega at(int r) const { return FinBicgOmega{ctl + r}; }
   __device__ void operator()(const double* t) const {
     double2 ts = make_double2(t[0], t[1]);
     double tt = t[2];
@@ -83,6 +88,7 @@ __device__ __forceinline__ void decide_update(SolverCtl* ctl, double rr, double 
 // BiCGstab end of iteration: |r|^2 and rho_new = <r_tilde, r>
 struct FinBicgIter {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinBicgIter at(int r) const { return FinBicgIter{ctl + r}; }
   __device__ void operator()(const double* t) const {
     if (ctl->done) { ctl_set_update(ctl, 0); return; }
     const double rr = t[0];
@@ -100,6 +106,7 @@ struct FinBicgIter {
 // BiCGstab reliable update (Alg. 2): t = {|r|^2 FP64, <r_tilde, r_hat>, |r_hat|^2}
 struct FinRelupBicg {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinRelupBicg at(int r) const { return FinRelupBicg{ctl + r}; }
   __device__ void operator()(const double* t) const {
     ctl->updates += 1;
     const double r2 = t[0];
@@ -119,6 +126,7 @@ struct FinRelupBicg {
 // BiCGstab setup: r_hat = r_tilde = quantised b_hat; t = {<r_t, r_hat>, |r_hat|^2}
 struct FinBicgSetup {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinBicgSetup at(int r) const { return FinBicgSetup{ctl + r}; }
   __device__ void operator()(const double* t) const {
     ctl->rho = make_double2(t[0], t[1]);
     ctl->rr = t[2];
@@ -129,6 +137,7 @@ struct FinBicgSetup {
 // CG: alpha = |r|^2 / <p, A p>, with <p, M^dag M p> = |M p|^2
 struct FinCgAlpha {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinCgAlpha at(int r) const { return FinCgAlpha{ctl + r}; }
   __device__ void operator()(const double* t) const {
     const double pap = t[0];
     if (!isfinite(pap)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
@@ -139,6 +148,7 @@ struct FinCgAlpha {
 
 struct FinCgIter {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinCgIter at(int r) const { return FinCgIter{ctl + r}; }
   __device__ void operator()(const double* t) const {
     if (ctl->done) { ctl_set_update(ctl, 0); return; }
     const double rr = t[0];
@@ -154,6 +164,7 @@ struct FinCgIter {
 // CG reliable update, first half: the FP64 Schur residual r = b_hat - M_hat x
 struct FinRelupCgR {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinRelupCgR at(int r) const { return FinRelupCgR{ctl + r}; }
   __device__ void operator()(const double* t) const {
     ctl->updates += 1;
     const double r2 = t[0];
@@ -171,6 +182,7 @@ struct FinRelupCgR {
 // uses beta = |r_hat_true|^2 / |r_hat_old|^2 (true residual in the numerator)
 struct FinRelupCgN {
   SolverCtl* ctl;
+  __device__ __forceinline__ FinRelupCgN at(int r) const { return FinRelupCgN{ctl + r}; }
   __device__ void operator()(const double* t) const {
     const double rr = t[0];
     if (!isfinite(rr)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
@@ -184,6 +196,7 @@ struct FinRelupCgN {
 struct FinCgSetup {
   SolverCtl* ctl;
   const double* bhat2;
+  __device__ __forceinline__ FinCgSetup at(int r) const { return FinCgSetup{ctl + r, bhat2 + r}; }
   __device__ void operator()(const double* t) const {
     ctl->rr = t[0];
     ctl->rr_prev = t[0];
@@ -201,6 +214,7 @@ template <class Out>
 struct EpiStore {
   static constexpr int NRED = 0;
   Out out;
+  __device__ __forceinline__ EpiStore at(int r) const { return EpiStore{out.at(r)}; }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double*) const { out.store(h, a); }
 };
@@ -212,6 +226,7 @@ struct EpiXpay {
   Out out;
   X x;
   Coef c;
+  __device__ __forceinline__ EpiXpay at(int r) const { return EpiXpay{out.at(r), x.at(r), c.at(r)}; }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double*) const {
     R xv[24];
@@ -233,6 +248,9 @@ struct EpiXpayDot {
   Coef c;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ EpiXpayDot at(int r) const {
+    return EpiXpayDot{out.at(r), x.at(r), w.at(r), c.at(r), rs, fin.at(r)};
+  }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
     R xv[24], wv[24];
@@ -242,14 +260,14 @@ struct EpiXpayDot {
     for (int k = 0; k < 24; ++k) a[k] = xv[k] + cc * a[k];
     out.store_get(h, a);
     w.load(h, wv);
-    double re = 0.0, im = 0.0;
+    R re = 0, im = 0;  // this site's 12 terms in the kernel's precision
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      re += (double)wv[2 * k] * a[2 * k] + (double)wv[2 * k + 1] * a[2 * k + 1];
-      im += (double)wv[2 * k] * a[2 * k + 1] - (double)wv[2 * k + 1] * a[2 * k];
+      re += wv[2 * k] * a[2 * k] + wv[2 * k + 1] * a[2 * k + 1];
+      im += wv[2 * k] * a[2 * k + 1] - wv[2 * k + 1] * a[2 * k];
     }
-    red[0] += re;
-    red[1] += im;
+    red[0] += (double)re;  // global sum in FP64
+    red[1] += (double)im;
   }
 };
 
@@ -262,6 +280,7 @@ struct EpiXpayTS {
   Coef c;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ EpiXpayTS at(int r) const { return EpiXpayTS{out.at(r), x.at(r), c.at(r), rs, fin.at(r)}; }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
     R sv[24];
@@ -270,17 +289,17 @@ struct EpiXpayTS {
 #pragma unroll
     for (int k = 0; k < 24; ++k) a[k] = sv[k] + cc * a[k];
     out.store_get(h, a);
-    double re = 0.0, im = 0.0, tt = 0.0;
+    R re = 0, im = 0, tt = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const double tr = a[2 * k], ti = a[2 * k + 1], sr = sv[2 * k], si = sv[2 * k + 1];
+      const R tr = a[2 * k], ti = a[2 * k + 1], sr = sv[2 * k], si = sv[2 * k + 1];
       re += tr * sr + ti * si;
       im += tr * si - ti * sr;
       tt += tr * tr + ti * ti;
     }
-    red[0] += re;
-    red[1] += im;
-    red[2] += tt;
+    red[0] += (double)re;
+    red[1] += (double)im;
+    red[2] += (double)tt;
   }
 };
 
@@ -293,6 +312,9 @@ struct EpiXpayNorm {
   Coef c;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ EpiXpayNorm at(int r) const {
+    return EpiXpayNorm{out.at(r), x.at(r), c.at(r), rs, fin.at(r)};
+  }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
     R xv[24];
@@ -301,10 +323,10 @@ struct EpiXpayNorm {
 #pragma unroll
     for (int k = 0; k < 24; ++k) a[k] = xv[k] + cc * a[k];
     out.store_get(h, a);
-    double n = 0.0;
+    R n = 0;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) n += (double)a[k] * a[k];
-    red[0] += n;
+    for (int k = 0; k < 24; ++k) n += a[k] * a[k];
+    red[0] += (double)n;
   }
 };
 
@@ -318,6 +340,9 @@ struct EpiCgUpdate {
   const SolverCtl* ctl;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ EpiCgUpdate at(int q) const {
+    return EpiCgUpdate{w.at(q), p.at(q), xh.at(q), r.at(q), c.at(q), ctl + q, rs, fin.at(q)};
+  }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
     const R al = (R)ctl->cg_alpha;
@@ -335,10 +360,10 @@ struct EpiCgUpdate {
     }
     xh.store(h, xv);
     r.store_get(h, rv);
-    double n = 0.0;
+    R n = 0;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) n += (double)rv[k] * rv[k];
-    red[0] += n;
+    for (int k = 0; k < 24; ++k) n += rv[k] * rv[k];
+    red[0] += (double)n;
   }
 };
 
@@ -354,20 +379,23 @@ struct EpiResid {
   Coef c;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ EpiResid at(int r) const {
+    return EpiResid{out.at(r), store, b.at(r), x.at(r), c.at(r), rs, fin.at(r)};
+  }
   template <typename R>
   __device__ __forceinline__ void operator()(int h, R (&a)[24], double* red) const {
     R bv[24], xv[24];
     b.load(h, bv);
     x.load(h, xv);
     const R cc = (R)c.get();
-    double n = 0.0;
+    R n = 0;
 #pragma unroll
     for (int k = 0; k < 24; ++k) {
       a[k] = bv[k] - (xv[k] + cc * a[k]);
-      n += (double)a[k] * a[k];
+      n += a[k] * a[k];
     }
     if (store) out.store(h, a);
-    red[0] += n;
+    red[0] += (double)n;
   }
 };
 
@@ -382,6 +410,9 @@ struct EpiRelupBicg {
   Coef c;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ EpiRelupBicg at(int r) const {
+    return EpiRelupBicg{b.at(r), x.at(r), rh.at(r), rt.at(r), c.at(r), rs, fin.at(r)};
+  }
   __device__ __forceinline__ void operator()(int h, double (&a)[24], double* red) const {
     double bv[24], xv[24];
     b.load(h, bv);
@@ -411,8 +442,18 @@ struct EpiRelupBicg {
 };
 
 // --------------------------------------------------------------- kernels
+// Resident blocks per SM the register allocation is held to (chosen from
+// ptxas register and spill counts): the FP32 and 16-bit kernels are
+// memory-latency bound and want warps, the fused-reduction epilogues need a
+// few more registers, and the FP64 kernel is bound by the FP64 pipe.
+template <typename R, class In, int NRED>
+struct DslashOccupancy {
+  static constexpr int kMinBlocks = (sizeof(R) == 8) ? 3 : In::kScaled ? (NRED == 0 ? 6 : 5) : (NRED == 0 ? 5 : 4);
+};
+
 template <bool DAGGER, typename R, class In, class G, class Epi>
-__global__ void __launch_bounds__(kDslashBlock) dslash_kernel(Geom g, In in, G gauge, int parity, Epi epi) {
+__global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRED>::kMinBlocks))
+    dslash_kernel(Geom g, In in, G gauge, int parity, Epi epi) {
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   double red[NR];
 #pragma unroll
@@ -455,6 +496,7 @@ struct OpBicgP {
   static constexpr int NRED = 0;
   S r, p, v;
   const SolverCtl* ctl;
+  __device__ __forceinline__ OpBicgP at(int q) const { return OpBicgP{r.at(q), p.at(q), v.at(q), ctl + q}; }
   __device__ __forceinline__ void operator()(int h, double*) const {
     using R = typename S::real;
     const double2 be = ctl->beta, om = ctl->omega;
@@ -477,6 +519,7 @@ struct OpBicgS {
   static constexpr int NRED = 0;
   S r, v;
   const SolverCtl* ctl;
+  __device__ __forceinline__ OpBicgS at(int q) const { return OpBicgS{r.at(q), v.at(q), ctl + q}; }
   __device__ __forceinline__ void operator()(int h, double*) const {
     using R = typename S::real;
     const double2 al = ctl->alpha;
@@ -496,6 +539,9 @@ struct OpBicgFinal {
   const SolverCtl* ctl;
   RedScratch rs;
   FinBicgIter fin;
+  __device__ __forceinline__ OpBicgFinal at(int q) const {
+    return OpBicgFinal{xh.at(q), p.at(q), r.at(q), t.at(q), rt.at(q), ctl + q, rs, fin.at(q)};
+  }
   __device__ __forceinline__ void operator()(int h, double* red) const {
     using R = typename S::real;
     const double2 al = ctl->alpha, om = ctl->omega;
@@ -510,17 +556,17 @@ struct OpBicgFinal {
     cmac<S>(sv, make_double2(-om.x, -om.y), tv);
     r.store_get(h, sv);
     rt.load(h, wv);
-    double n = 0.0, re = 0.0, im = 0.0;
+    R n = 0, re = 0, im = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const double a = sv[2 * k], b = sv[2 * k + 1], wr = wv[2 * k], wi = wv[2 * k + 1];
+      const R a = sv[2 * k], b = sv[2 * k + 1], wr = wv[2 * k], wi = wv[2 * k + 1];
       n += a * a + b * b;
       re += wr * a + wi * b;
       im += wr * b - wi * a;
     }
-    red[0] += n;
-    red[1] += re;
-    red[2] += im;
+    red[0] += (double)n;
+    red[1] += (double)re;
+    red[2] += (double)im;
   }
 };
 
@@ -530,6 +576,7 @@ struct OpCgP {
   static constexpr int NRED = 0;
   S r, p;
   const SolverCtl* ctl;
+  __device__ __forceinline__ OpCgP at(int q) const { return OpCgP{r.at(q), p.at(q), ctl + q}; }
   __device__ __forceinline__ void operator()(int h, double*) const {
     using R = typename S::real;
     const R be = (R)ctl->beta.x;
@@ -548,6 +595,7 @@ struct OpAccumulate {
   static constexpr int NRED = 0;
   SpinorF64 x;
   S xh;
+  __device__ __forceinline__ OpAccumulate at(int r) const { return OpAccumulate{x.at(r), xh.at(r)}; }
   __device__ __forceinline__ void operator()(int h, double*) const {
     double xv[24], hv[24];
     x.load(h, xv);
@@ -568,6 +616,7 @@ struct OpConvert {
   static constexpr int NRED = 0;
   Out out;
   In in;
+  __device__ __forceinline__ OpConvert at(int r) const { return OpConvert{out.at(r), in.at(r)}; }
   __device__ __forceinline__ void operator()(int h, double*) const {
     using R = typename In::real;
     R v[24];
@@ -584,6 +633,9 @@ struct OpQuantDup {
   In in;
   RedScratch rs;
   Fin fin;
+  __device__ __forceinline__ OpQuantDup at(int r) const {
+    return OpQuantDup{out1.at(r), out2.at(r), in.at(r), rs, fin.at(r)};
+  }
   __device__ __forceinline__ void operator()(int h, double* red) const {
     double v[24], v2[24];
     in.load(h, v);
@@ -605,11 +657,12 @@ struct OpNorm2 {
   S in;
   RedScratch rs;
   FinStore fin;
+  __device__ __forceinline__ OpNorm2 at(int r) const { return OpNorm2{in.at(r), rs, fin.at(r)}; }
   __device__ __forceinline__ void operator()(int h, double* red) const {
     using R = typename S::real;
     R v[24];
     in.load(h, v);
-    double n = 0.0;
+    double n = 0.0;  // API norm: every square accumulated in FP64 (not on the solver path)
 #pragma unroll
     for (int k = 0; k < 24; ++k) n += (double)v[k] * v[k];
     red[0] += n;
@@ -620,6 +673,7 @@ template <class S>
 struct OpZero {
   static constexpr int NRED = 0;
   S out;
+  __device__ __forceinline__ OpZero at(int r) const { return OpZero{out.at(r)}; }
   __device__ __forceinline__ void operator()(int h, double*) const {
     float z[24];
 #pragma unroll
@@ -682,7 +736,7 @@ struct Tr<WD_F64> {
   using G = GaugeF64;
   using R = double;
   static size_t bytes(int stride) { return align256(192 * (size_t)stride); }
-  static S view(const void* p, const Geom& g) { return S{(double2*)p, g.stride}; }
+  static S view(const void* p, const Geom& g, size_t rs = 0) { return S{(double2*)p, g.stride, rs}; }
   static G gauge(const Ctx& c) { return G{(const double2*)c.gauge[WD_F64], c.g.stride, c.recon}; }
 };
 template <>
@@ -691,7 +745,7 @@ struct Tr<WD_F32> {
   using G = GaugeF32;
   using R = float;
   static size_t bytes(int stride) { return align256(96 * (size_t)stride); }
-  static S view(const void* p, const Geom& g) { return S{(float4*)p, g.stride}; }
+  static S view(const void* p, const Geom& g, size_t rs = 0) { return S{(float4*)p, g.stride, rs}; }
   static G gauge(const Ctx& c) { return G{(const float4*)c.gauge[WD_F32], c.g.stride}; }
 };
 template <Fmt16 F, int P>
@@ -700,8 +754,8 @@ struct Tr16 {
   using G = Gauge16<F>;
   using R = float;
   static size_t bytes(int stride) { return align256(48 * (size_t)stride) + align256(4 * (size_t)stride); }
-  static S view(const void* p, const Geom& g) {
-    return S{(uint4*)p, (float*)((char*)p + align256(48 * (size_t)g.stride)), g.stride};
+  static S view(const void* p, const Geom& g, size_t rs = 0) {
+    return S{(uint4*)p, (float*)((char*)p + align256(48 * (size_t)g.stride)), g.stride, rs};
   }
   static G gauge(const Ctx& c) { return G{(const uint4*)c.gauge[P], (const uint2*)c.gauge4[P], c.g.stride}; }
 };

@@ -92,14 +92,7 @@ extern "C" wd_status wd_norm2_noalloc(double* result, const void* field, const i
             "65536 partial sums)");
     return WD_ERR_INVALID_ARG;
   }
-  Geom g{};
-  g.X = dims[0];
-  g.Y = dims[1];
-  g.Z = dims[2];
-  g.T = dims[3];
-  g.Xh = dims[0] / 2;
-  g.Vh = (int)vh;
-  g.stride = round_up(g.Vh, 32);
+  const Geom g = make_geom(dims, 0);
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess || device < 0 || device >= kMaxDevices) {

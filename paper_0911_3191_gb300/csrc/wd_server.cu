@@ -1,0 +1,525 @@
+// Serving: continuous batching of solve requests (C ABI wd_server_*).
+//
+// Requests (a source b, kappa, tol) arrive for one of several resident gauge
+// fields, possibly of different lattice volumes.  Each gauge field has a pool:
+// its own context and CUDA stream, and -- while it has work -- a batch of
+// solver slots in one device allocation, iterated in lockstep by the batched
+// reliable-update BiCGstab (wd_batch.cuh) as a CUDA graph that pauses every
+// `iters_per_step` iterations.  Between steps the host retires converged
+// slots (FP64 reconstruction and true residual on the device, solution copied
+// to the caller's buffer), admits queued requests into free slots (setup of
+// one slot while the others keep their Krylov state), and releases the slot
+// memory of idle pools so that other pools can grow.  Every allocation is
+// charged against a device-memory budget; pools on different streams overlap
+// on the device.  A request's iteration is the same kernel sequence whether it
+// runs alone or in a mix, so its result does not depend on its neighbours
+// beyond rounding of the reductions' block partition.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "wd_batch.cuh"
+
+using namespace wd;
+
+namespace {
+
+struct Request {
+  long long id;
+  int pool;
+  const double* b;
+  double* x;
+  double kappa, tol;
+  int state;  // 0 queued, 1 active, 2 finished
+  int slot;
+  wd_solve_info info;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Pool {
+  wd_ctx* ctx = nullptr;
+  int dims[4] = {0, 0, 0, 0};
+  size_t fixed_bytes = 0;  // gauge copies, staging, scratch
+  int capacity = 0;        // slots (0: no workspace)
+  void* ws = nullptr;      // slot fields
+  void* small = nullptr;   // ctl array, BatchCtl, partials, kappas, scalars
+  size_t ws_bytes = 0;
+  BatchBufs bb{};
+  void* bfull = nullptr;   // per slot FP64 full source field (inside ws)
+  BatchLaunch bl{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long hu = 0, hl = 0;
+  std::vector<long long> slot_req;  // -1 free
+  std::deque<long long> queue;
+  SolverCtl* hctl = nullptr;        // pinned mirror of the ctl array
+  double* hscal = nullptr;          // pinned mirror of per-slot scalars
+  bool launched = false;
+};
+
+}  // namespace
+
+struct wd_server {
+  wd_server_params p;
+  std::vector<Pool> pools;
+  std::map<long long, Request> reqs;
+  size_t used = 0;
+  long long next_id = 1;
+  std::string err;
+};
+
+namespace {
+
+wd_status serr(wd_server* s, wd_status st, const std::string& m) {
+  if (s) s->err = m;
+  return st;
+}
+
+#define WS_CK(s, call)                                                                                    \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess)                                                                                \
+      return serr(s, e_ == cudaErrorMemoryAllocation ? WD_ERR_OOM : WD_ERR_CUDA,                          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                    \
+  } while (0)
+
+size_t fbytes(const Ctx& c, int prec) { return prec_ops(prec)->field_bytes(c.g.stride); }
+
+size_t slot_bytes(const Ctx& c, int prec) {
+  return 2 * fbytes(c, WD_F64) + 3 * fbytes(c, WD_F64) + 7 * fbytes(c, prec);
+}
+
+int blas_gx_for(const Ctx& c, int n) {
+  const int per = (c.num_sms * 8 + n - 1) / n;
+  const int need = (c.g.Vh + kBlasBlock - 1) / kBlasBlock;
+  return std::max(1, std::min(per, need));
+}
+
+size_t small_bytes(const Ctx& c, int n) {
+  const int maxblk = std::max(c.num_sms * 16, blas_gx_for(c, n));
+  return align256((size_t)n * sizeof(SolverCtl)) + align256(sizeof(BatchCtl)) +
+         align256((size_t)maxblk * n * 4 * sizeof(double)) + align256((size_t)2 * n * 8) + align256((size_t)4 * n * 8);
+}
+
+__global__ void slot_init_kernel(SolverCtl* ctl, double tol, double delta, int max_iter, double kappa,
+                                 const double* bnorm2) {
+  SolverCtl c;
+  memset(&c, 0, sizeof(c));
+  c.rho = c.rho_prev = c.alpha = c.omega = make_double2(1.0, 0.0);
+  c.beta = make_double2(0.0, 0.0);
+  const double b2 = bnorm2[0] + bnorm2[1];
+  c.stop2 = tol * tol * b2;
+  c.delta = delta;
+  c.kappa = kappa;
+  c.neg_kappa2 = -kappa * kappa;
+  c.max_iter = max_iter;
+  c.status = WD_OK;
+  if (!isfinite(b2)) {
+    c.status = WD_ERR_NUMERIC;
+    c.done = 1;
+  } else if (b2 == 0.0) {
+    c.done = 1;
+  }
+  *ctl = c;
+}
+
+__global__ void mark_free_kernel(SolverCtl* ctl, int n) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) {
+    ctl[r].done = 1;
+    ctl[r].do_update = 0;
+  }
+}
+
+__global__ void batch_reset_kernel(BatchCtl* bc, int step_limit, int in_graph, unsigned long long hu,
+                                   unsigned long long hl) {
+  for (int k = 0; k < 4; ++k) bc->counter[k] = 0;
+  bc->any_update = 0;
+  bc->all_done = 0;
+  bc->in_graph = in_graph;
+  bc->loops = 0;
+  bc->max_loops = 1 << 30;  // slots carry their own max_iter
+  bc->step_loops = 0;
+  bc->step_limit = step_limit;
+  bc->h_update = hu;
+  bc->h_loop = hl;
+}
+
+void release_workspace(Pool& pl, size_t& used) {
+  if (pl.exec) cudaGraphExecDestroy(pl.exec);
+  if (pl.graph) cudaGraphDestroy(pl.graph);
+  pl.exec = nullptr;
+  pl.graph = nullptr;
+  if (pl.ws) cudaFree(pl.ws);
+  if (pl.small) cudaFree(pl.small);
+  if (pl.hctl) cudaFreeHost(pl.hctl);
+  pl.ws = pl.small = nullptr;
+  pl.hctl = nullptr;
+  pl.hscal = nullptr;
+  used -= pl.ws_bytes;
+  pl.ws_bytes = 0;
+  pl.capacity = 0;
+  pl.slot_req.clear();
+}
+
+// Workspace for `cap` slots: the batch views of wd_batch.cuh plus one FP64
+// full source field per slot.
+wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
+  Ctx& c = pl.ctx->c;
+  const int prec = sv->p.inner_precision;
+  const size_t f64 = fbytes(c, WD_F64), fin = fbytes(c, prec);
+  const size_t ws = slot_bytes(c, prec) * cap, sm = small_bytes(c, cap);
+  WS_CK(sv, cudaMalloc(&pl.ws, ws));
+  if (cudaMalloc(&pl.small, sm) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(pl.ws);
+    pl.ws = nullptr;
+    return serr(sv, WD_ERR_OOM, "slot control allocation failed");
+  }
+  WS_CK(sv, cudaMemset(pl.small, 0, sm));
+  WS_CK(sv, cudaMallocHost((void**)&pl.hctl, (size_t)cap * sizeof(SolverCtl) + 4 * (size_t)cap * 8 + 64));
+  pl.hscal = (double*)((char*)pl.hctl + (size_t)cap * sizeof(SolverCtl));
+  pl.ws_bytes = ws + sm;
+  sv->used += pl.ws_bytes;
+  pl.capacity = cap;
+  pl.slot_req.assign(cap, -1);
+  // carve the views
+  char* s = (char*)pl.small;
+  BatchBufs& b = pl.bb;
+  b.ctl = (SolverCtl*)s;
+  s += align256((size_t)cap * sizeof(SolverCtl));
+  b.bc = (BatchCtl*)s;
+  s += align256(sizeof(BatchCtl));
+  b.partials = (double*)s;
+  s += align256((size_t)std::max(c.num_sms * 16, blas_gx_for(c, cap)) * cap * 4 * sizeof(double));
+  b.kappas = (double*)s;
+  s += align256((size_t)2 * cap * 8);
+  b.scal = (double*)s;
+  char* p = (char*)pl.ws;
+  pl.bfull = p; p += 2 * f64 * cap;
+  b.b_hat = p; p += f64 * cap;
+  b.xe = p; p += f64 * cap;
+  b.tmp64 = p; p += f64 * cap;
+  b.r_hat = p; p += fin * cap;
+  b.r_tilde = p; p += fin * cap;
+  b.p = p; p += fin * cap;
+  b.v = p; p += fin * cap;
+  b.t = p; p += fin * cap;
+  b.x_hat = p; p += fin * cap;
+  b.tmp = p; p += fin * cap;
+  const int ntiles = (c.g.Vh + 31) / 32;
+  pl.bl = BatchLaunch{cap, 4, std::min(c.num_sms * 4, ntiles), blas_gx_for(c, cap)};
+  mark_free_kernel<<<(cap + 127) / 128, 128, 0, c.stream>>>(b.ctl, cap);
+  WS_CK(sv, cudaGetLastError());
+  if (sv->p.use_graph) {
+    cudaError_t e = build_batch_loop_graph(c, prec, b, pl.bl, &pl.graph, &pl.exec, &pl.hu, &pl.hl);
+    if (e != cudaSuccess) return serr(sv, WD_ERR_CUDA, std::string("pool graph: ") + cudaGetErrorString(e));
+  }
+  WS_CK(sv, cudaStreamSynchronize(c.stream));
+  return WD_OK;
+}
+
+// single-slot views (batch fields at slot r)
+SolveBufs slot_bufs(Pool& pl, int r, int prec) {
+  Ctx& c = pl.ctx->c;
+  const size_t f64 = fbytes(c, WD_F64), fin = fbytes(c, prec);
+  SolveBufs s{};
+  s.ctl = pl.bb.ctl + r;
+  s.b_hat = (char*)pl.bb.b_hat + r * f64;
+  s.x = (char*)pl.bb.xe + r * f64;
+  s.r = nullptr;
+  s.tmp64 = (char*)pl.bb.tmp64 + r * f64;
+  s.r_hat = (char*)pl.bb.r_hat + r * fin;
+  s.r_tilde = (char*)pl.bb.r_tilde + r * fin;
+  s.p = (char*)pl.bb.p + r * fin;
+  s.v = (char*)pl.bb.v + r * fin;
+  s.t = (char*)pl.bb.t + r * fin;
+  s.x_hat = (char*)pl.bb.x_hat + r * fin;
+  s.tmp = (char*)pl.bb.tmp + r * fin;
+  return s;
+}
+
+// admission of one request into slot r: source upload, Schur source, control
+// block, quantised residual; the other slots keep their Krylov state
+wd_status admit(wd_server* sv, Pool& pl, Request& q, int r) {
+  Ctx& c = pl.ctx->c;
+  const int prec = sv->p.inner_precision;
+  const size_t f64 = fbytes(c, WD_F64);
+  char* bf = (char*)pl.bfull + 2 * f64 * r;
+  wd_status st = wd_field_import(pl.ctx, bf, q.b, 0, WD_EVEN, WD_F64);
+  if (st == WD_OK) st = wd_field_import(pl.ctx, bf + f64, q.b, 0, WD_ODD, WD_F64);
+  if (st != WD_OK) return serr(sv, st, std::string("source upload: ") + wd_last_error(pl.ctx));
+  const PrecOps* o64 = ops_f64();
+  SolveBufs s = slot_bufs(pl, r, prec);
+  double* sc = pl.bb.scal + 4 * r;
+  o64->norm2(c, sc + 0, bf, c.stream);
+  o64->norm2(c, sc + 1, bf + f64, c.stream);
+  o64->dslash_xpay(c, s.b_hat, bf + f64, bf, q.kappa, nullptr, 0, 0, c.stream);
+  o64->zero(c, s.x, c.stream);
+  slot_init_kernel<<<1, 1, 0, c.stream>>>(s.ctl, q.tol, prec == WD_F64 ? 0.0 : sv->p.delta, sv->p.max_iter, q.kappa,
+                                          sc);
+  prec_ops(prec)->bicg_setup(c, s, c.stream);
+  WS_CK(sv, cudaGetLastError());
+  pl.slot_req[r] = q.id;
+  q.state = 1;
+  q.slot = r;
+  return WD_OK;
+}
+
+// retirement of slot r: x_e, x_o = b_o + kappa D_oe x_e, the full FP64 true
+// residual, and the solution copied to the caller's host buffer
+wd_status retire(wd_server* sv, Pool& pl, Request& q, int r, const SolverCtl& hc) {
+  Ctx& c = pl.ctx->c;
+  const int prec = sv->p.inner_precision;
+  const size_t f64 = fbytes(c, WD_F64);
+  const char* bf = (const char*)pl.bfull + 2 * f64 * r;
+  SolveBufs s = slot_bufs(pl, r, prec);
+  using T64 = Tr<WD_F64>;
+  const Geom& g = c.g;
+  ops_f64()->dslash_xpay(c, s.tmp64, s.x, bf + f64, q.kappa, nullptr, 1, 0, c.stream);  // x_o in tmp64
+  double* sc = pl.bb.scal + 4 * r;
+  const Coef ck{-q.kappa, nullptr};
+  EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> ee{T64::view(nullptr, g), false, T64::view(bf, g),
+                                                         T64::view(s.x, g), ck, c.red, FinStore{sc + 2, 1}};
+  launch_dslash<double>(c, T64::view(s.tmp64, g), T64::gauge(c), 0, 0, ee, c.stream);
+  EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> eo{T64::view(nullptr, g), false, T64::view(bf + f64, g),
+                                                         T64::view(s.tmp64, g), ck, c.red, FinStore{sc + 3, 1}};
+  launch_dslash<double>(c, T64::view(s.x, g), T64::gauge(c), 1, 0, eo, c.stream);
+  WS_CK(sv, cudaGetLastError());
+  WS_CK(sv, cudaMemcpyAsync(pl.hscal + 4 * r, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  // export both parities of x, then one copy to the caller
+  const wd_status st = wd_internal_export_full(pl.ctx, q.x, s.x, s.tmp64);
+  if (st != WD_OK) return serr(sv, st, std::string("solution download: ") + wd_last_error(pl.ctx));
+  const double* h = pl.hscal + 4 * r;
+  const double b2 = h[0] + h[1], r2 = h[2] + h[3];
+  wd_status rs = (wd_status)hc.status;
+  if (rs == WD_OK && !hc.done) rs = WD_ERR_NOT_CONVERGED;
+  if (b2 > 0.0 && !std::isfinite(r2)) rs = WD_ERR_NUMERIC;
+  q.info.iters = hc.iter + hc.updates;
+  q.info.reliable_updates = hc.updates;
+  q.info.true_rel_residual = b2 > 0.0 ? std::sqrt(r2 / b2) : 0.0;
+  q.info.iterated_rel_residual = b2 > 0.0 ? std::sqrt(hc.rr / b2) : 0.0;
+  q.info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - q.t_submit).count();
+  q.info.status = rs;
+  q.info.kernel_launches = 0;
+  q.state = 2;
+  pl.slot_req[r] = -1;
+  mark_free_kernel<<<1, 1, 0, c.stream>>>(pl.bb.ctl + r, 1);
+  WS_CK(sv, cudaGetLastError());
+  return WD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wd_status wd_server_create(wd_server** out, const wd_server_params* p) {
+  if (!out || !p) return WD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (p->max_slots < 1 || p->max_slots > 256 || p->iters_per_step < 1 || p->inner_precision < WD_F64 ||
+      p->inner_precision > WD_B16N || p->max_iter < 1)
+    return WD_ERR_INVALID_ARG;
+  if (p->inner_precision != WD_F64 && !(p->delta > 0.0 && p->delta < 1.0)) return WD_ERR_INVALID_ARG;
+  wd_server* s = new (std::nothrow) wd_server();
+  if (!s) return WD_ERR_OOM;
+  s->p = *p;
+  *out = s;
+  return WD_OK;
+}
+
+wd_status wd_server_destroy(wd_server* s) {
+  if (!s) return WD_OK;
+  for (Pool& pl : s->pools) {
+    if (pl.ctx) cudaStreamSynchronize(pl.ctx->c.stream);
+    release_workspace(pl, s->used);
+    if (pl.ctx) {
+      cudaStream_t st = pl.ctx->c.stream;
+      wd_destroy(pl.ctx);
+      if (st) cudaStreamDestroy(st);
+    }
+  }
+  delete s;
+  return WD_OK;
+}
+
+const char* wd_server_last_error(const wd_server* s) { return s ? s->err.c_str() : "null server"; }
+
+wd_status wd_server_add_gauge(wd_server* s, const int dims[4], int t_antiperiodic, const double* U, int recon,
+                              int* gauge_id) {
+  if (!s || !dims || !U || !gauge_id) return serr(s, WD_ERR_INVALID_ARG, "wd_server_add_gauge: bad args");
+  cudaStream_t st;
+  WS_CK(s, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  Pool pl;
+  wd_status r = wd_create(&pl.ctx, dims, t_antiperiodic, st);
+  if (r != WD_OK) {
+    cudaStreamDestroy(st);
+    return serr(s, r, "wd_server_add_gauge: bad lattice");
+  }
+  Ctx& c = pl.ctx->c;
+  memcpy(pl.dims, dims, sizeof(pl.dims));
+  // resident cost: FP64 and inner gauge copies, staging of one host field,
+  // scratch; charged before anything is allocated
+  const size_t links = (size_t)8 * c.g.stride;
+  size_t inner_gauge = 0;
+  const int ip = s->p.inner_precision;
+  if (ip == WD_F32) inner_gauge = links * 48;
+  else if (ip != WD_F64) inner_gauge = links * 24;
+  pl.fixed_bytes = links * (recon / 2) * 16 + inner_gauge + (size_t)2 * c.g.Vh * 24 * 8 + ((size_t)c.num_sms * 128 * 8);
+  if (s->p.budget_bytes && s->used + pl.fixed_bytes > s->p.budget_bytes) {
+    wd_destroy(pl.ctx);
+    cudaStreamDestroy(st);
+    return serr(s, WD_ERR_BUDGET, "gauge field does not fit the memory budget");
+  }
+  r = wd_load_gauge(pl.ctx, U, 0, recon);
+  if (r == WD_OK) r = wd_internal_ensure_gauge(pl.ctx, ip);
+  if (r != WD_OK) {
+    std::string m = wd_last_error(pl.ctx);
+    wd_destroy(pl.ctx);
+    cudaStreamDestroy(st);
+    return serr(s, r, "wd_server_add_gauge: " + m);
+  }
+  s->used += pl.fixed_bytes;
+  s->pools.push_back(std::move(pl));
+  *gauge_id = (int)s->pools.size() - 1;
+  return WD_OK;
+}
+
+wd_status wd_server_submit(wd_server* s, int gauge_id, const double* b, double* x, double kappa, double tol,
+                           long long* request_id) {
+  if (!s || !b || !x || !request_id || gauge_id < 0 || gauge_id >= (int)s->pools.size() || !(tol > 0.0) ||
+      !std::isfinite(kappa))
+    return serr(s, WD_ERR_INVALID_ARG, "wd_server_submit: bad args");
+  {
+    // a request whose single slot could never fit the budget is refused now
+    const Pool& pl = s->pools[gauge_id];
+    size_t fixed = 0;
+    for (const Pool& q : s->pools) fixed += q.fixed_bytes;
+    if (s->p.budget_bytes &&
+        fixed + slot_bytes(pl.ctx->c, s->p.inner_precision) + small_bytes(pl.ctx->c, 1) > s->p.budget_bytes)
+      return serr(s, WD_ERR_BUDGET, "one solver slot for this lattice exceeds the memory budget");
+  }
+  Request q{};
+  q.id = s->next_id++;
+  q.pool = gauge_id;
+  q.b = b;
+  q.x = x;
+  q.kappa = kappa;
+  q.tol = tol;
+  q.state = 0;
+  q.slot = -1;
+  q.t_submit = std::chrono::steady_clock::now();
+  s->reqs[q.id] = q;
+  s->pools[gauge_id].queue.push_back(q.id);
+  *request_id = q.id;
+  return WD_OK;
+}
+
+wd_status wd_server_step(wd_server* s, int* active_out, int* queued_out) {
+  if (!s) return WD_ERR_INVALID_ARG;
+  const int prec = s->p.inner_precision;
+  // 1. retire slots whose system finished during the last step
+  for (Pool& pl : s->pools) {
+    if (!pl.capacity || !pl.launched) continue;
+    Ctx& c = pl.ctx->c;
+    WS_CK(s, cudaMemcpyAsync(pl.hctl, pl.bb.ctl, pl.capacity * sizeof(SolverCtl), cudaMemcpyDeviceToHost, c.stream));
+    WS_CK(s, cudaStreamSynchronize(c.stream));
+    for (int r = 0; r < pl.capacity; ++r) {
+      if (pl.slot_req[r] < 0) continue;
+      if (!pl.hctl[r].done) continue;
+      wd_status st = retire(s, pl, s->reqs[pl.slot_req[r]], r, pl.hctl[r]);
+      if (st != WD_OK) return st;
+    }
+    WS_CK(s, cudaStreamSynchronize(c.stream));
+    pl.launched = false;
+  }
+  // 2. release the slot memory of idle pools
+  for (Pool& pl : s->pools) {
+    if (!pl.capacity || !pl.queue.empty()) continue;
+    bool busy = false;
+    for (long long id : pl.slot_req) busy |= (id >= 0);
+    if (!busy) release_workspace(pl, s->used);
+  }
+  // 3. admit queued requests into free slots while memory allows; pools that
+  // need slot memory share what the budget has left equally
+  int waiting = 0;
+  for (Pool& pl : s->pools) waiting += (!pl.queue.empty() && !pl.capacity);
+  for (Pool& pl : s->pools) {
+    if (pl.queue.empty()) continue;
+    if (!pl.capacity) {
+      const size_t left = s->p.budget_bytes ? (s->p.budget_bytes > s->used ? s->p.budget_bytes - s->used : 0)
+                                            : (size_t)-1;
+      const size_t share = s->p.budget_bytes ? left / (size_t)std::max(1, waiting) : left;
+      int cap = s->p.max_slots;
+      while (cap > 0 && s->p.budget_bytes &&
+             slot_bytes(pl.ctx->c, prec) * cap + small_bytes(pl.ctx->c, cap) > share)
+        --cap;
+      if (cap < 1 && share < left && s->p.budget_bytes &&
+          slot_bytes(pl.ctx->c, prec) + small_bytes(pl.ctx->c, 1) <= left)
+        cap = 1;
+      if (cap < 1) continue;  // waits until another pool frees memory
+      --waiting;
+      wd_status st = alloc_workspace(s, pl, cap);
+      if (st != WD_OK) return st;
+    }
+    for (int r = 0; r < pl.capacity && !pl.queue.empty(); ++r) {
+      if (pl.slot_req[r] >= 0) continue;
+      const long long id = pl.queue.front();
+      pl.queue.pop_front();
+      wd_status st = admit(s, pl, s->reqs[id], r);
+      if (st != WD_OK) return st;
+    }
+  }
+  // 4. run up to iters_per_step lockstep iterations on every busy pool; the
+  // pools' streams run concurrently
+  int active = 0, queued = 0;
+  for (Pool& pl : s->pools) {
+    queued += (int)pl.queue.size();
+    int n = 0;
+    for (long long id : pl.slot_req) n += (id >= 0);
+    active += n;
+    if (!n) continue;
+    Ctx& c = pl.ctx->c;
+    batch_reset_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, s->p.iters_per_step, s->p.use_graph ? 1 : 0, pl.hu, pl.hl);
+    WS_CK(s, cudaGetLastError());
+    if (s->p.use_graph) {
+      WS_CK(s, cudaGraphLaunch(pl.exec, c.stream));
+    } else {
+      const PrecOps* o = prec_ops(prec);
+      BatchCtl hb;
+      for (int it = 0; it < s->p.iters_per_step; ++it) {
+        o->batch_iteration(c, pl.bl, pl.bb, c.stream);
+        WS_CK(s, cudaMemcpyAsync(&hb, pl.bb.bc, sizeof(hb), cudaMemcpyDeviceToHost, c.stream));
+        WS_CK(s, cudaStreamSynchronize(c.stream));
+        if (hb.any_update) o->batch_update(c, pl.bl, pl.bb, c.stream);
+        batch_loop_control_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, pl.bb.ctl, pl.capacity);
+        WS_CK(s, cudaMemcpyAsync(&hb, pl.bb.bc, sizeof(hb), cudaMemcpyDeviceToHost, c.stream));
+        WS_CK(s, cudaStreamSynchronize(c.stream));
+        if (hb.all_done) break;
+      }
+    }
+    pl.launched = true;
+  }
+  for (Pool& pl : s->pools)
+    if (pl.launched) WS_CK(s, cudaStreamSynchronize(pl.ctx->c.stream));
+  if (active_out) *active_out = active;
+  if (queued_out) *queued_out = queued;
+  return WD_OK;
+}
+
+wd_status wd_server_poll(wd_server* s, long long request_id, int* finished, wd_solve_info* info) {
+  if (!s || !finished) return WD_ERR_INVALID_ARG;
+  auto it = s->reqs.find(request_id);
+  if (it == s->reqs.end()) return serr(s, WD_ERR_INVALID_ARG, "unknown request id");
+  *finished = it->second.state == 2;
+  if (*finished && info) *info = it->second.info;
+  return WD_OK;
+}
+
+size_t wd_server_memory_in_use(const wd_server* s) { return s ? s->used : 0; }
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+"""Continuous-batching server (wd_server_*): requests of several lattice
+volumes, kappas and tolerances, admitted as slots and memory free up, run
+concurrently; every result is checked by the FP64 CPU oracle and must equal
+the same solve done alone, within the solver tolerance."""
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fields():
+    a = (8, 8, 8, 16)
+    b = (4, 6, 8, 10)
+    return {a: li.gauge(a, 0.5, 1020), b: li.gauge(b, 0.5, 1021)}
+
+
+def _drain(srv, ids, max_steps=100000):
+    done = {}
+    for _ in range(max_steps):
+        active, queued = srv.step()
+        for rid in list(ids):
+            f, res, x = srv.poll(rid)
+            if f:
+                done[rid] = (res, x)
+                ids.remove(rid)
+        if not ids:
+            return done
+    raise AssertionError("requests did not finish")
+
+
+def test_mixed_requests_match_solo_solves(fields):
+    import paper_0911_3191_gb300 as m
+    srv = m.Server(max_slots=4, iters_per_step=5, inner_precision=m.Q16)
+    gids = {dims: srv.add_gauge(dims, U) for dims, U in fields.items()}
+    rng = np.random.default_rng(7)
+    reqs = []
+    for k in range(9):
+        dims = list(fields)[k % 2]
+        b = li.gaussian_spinor(dims, 2200 + k)
+        kappa = float(rng.uniform(0.115, 0.124))
+        tol = [1e-8, 1e-10, 1e-12][k % 3]
+        rid = srv.submit(gids[dims], b, kappa, tol)
+        reqs.append((rid, dims, b, kappa, tol))
+    # more arrivals while the first ones are running
+    srv.step()
+    for k in range(9, 13):
+        dims = list(fields)[k % 2]
+        b = li.gaussian_spinor(dims, 2200 + k)
+        rid = srv.submit(gids[dims], b, 0.12, 1e-12)
+        reqs.append((rid, dims, b, 0.12, 1e-12))
+    done = _drain(srv, [r[0] for r in reqs])
+    for rid, dims, b, kappa, tol in reqs:
+        res, x = done[rid]
+        rel = oracle.true_residual(x, b, fields[dims], dims, kappa)
+        assert res.status == 0 and rel <= tol, (rid, res, rel)
+        solo = m.WilsonDirac(dims)
+        solo.load_gauge(fields[dims])
+        x1 = np.zeros_like(b)
+        r1 = solo.solve(x1, b, kappa, tol=tol, inner_precision=m.Q16)
+        assert r1.status == 0
+        # the same result alone and in the mix, within the requested tolerance
+        assert np.linalg.norm(x - x1) / np.linalg.norm(x1) <= 200 * tol
+        solo.close()
+    srv.close()
+
+
+def test_budget_admits_as_memory_frees(fields):
+    """A budget that holds the gauge fields and one solver slot: requests
+    queue and are admitted one at a time, all finish."""
+    import paper_0911_3191_gb300 as m
+    dims = (8, 8, 8, 16)
+    probe = m.Server(max_slots=1, inner_precision=m.F32)
+    gid = probe.add_gauge(dims, fields[dims])
+    fixed = probe.memory_in_use()
+    probe.close()
+    vh = li.volume(dims) // 2
+    # one slot: 5 FP64 fields (source, Schur source, solution, residual work)
+    # + 7 FP32 Krylov fields + control (~80 KB); two slots do not fit
+    slot = 5 * 192 * vh + 7 * 96 * vh + 256 * 1024
+    srv = m.Server(budget_bytes=fixed + slot, max_slots=4, iters_per_step=10, inner_precision=m.F32)
+    gid = srv.add_gauge(dims, fields[dims])
+    ids = []
+    bs = {}
+    for k in range(3):
+        b = li.gaussian_spinor(dims, 2300 + k)
+        rid = srv.submit(gid, b, 0.12, 1e-10)
+        ids.append(rid)
+        bs[rid] = b
+    active, queued = srv.step()
+    assert active == 1 and queued == 2
+    assert srv.memory_in_use() <= fixed + slot
+    done = _drain(srv, list(ids))
+    for rid in ids:
+        res, x = done[rid]
+        assert res.status == 0
+        assert oracle.true_residual(x, bs[rid], fields[dims], dims, 0.12) <= 1e-10
+    srv.close()
+
+
+def test_budget_too_small_is_refused(fields):
+    import paper_0911_3191_gb300 as m
+    dims = (8, 8, 8, 16)
+    srv = m.Server(budget_bytes=1024, max_slots=2)
+    with pytest.raises(m.WDError) as e:
+        srv.add_gauge(dims, fields[dims])
+    assert e.value.status == 8  # WD_ERR_BUDGET
+    srv.close()
