@@ -45,6 +45,17 @@ METRIC = "dslash GB/s vs HBM peak; mixed vs FP64 solve time to |r|/|b|<=1e-12"
 BYTES_PER_SITE = {0: 8 * 96 + 192 + 192, 1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 52, 3: 8 * 24 + 52 + 52,
                   4: 8 * 24 + 52 + 52}
 FLOPS_PER_SITE = 1320  # the paper's effective count (Sec. 4.3)
+# FP64 FMA peak of one GB300, measured with an FMA-throughput loop (1.252 TFLOP/s);
+# the unit count agrees: 2 FP64 FMA lanes per SM per clock x 2 flops x 152 SMs
+# x 2.07 GHz = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 1.252
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# ncu capture of the current kernels (profiles/dslash_f64_18real_24x24x24x64_ncu_full.md);
+# keyed by (precision, link reals, lattice); to be set to None when a kernel changes
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --set full,
+# the dslash-only command of this file at 24^3x64); None where not captured
+# since the kernel last changed.
+NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64"): 650.13e6, ("q16", 12, "24x24x24x64"): 112.31e6}
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
 
@@ -135,7 +146,8 @@ def max_over_ranks(ws, v: float) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -277,6 +289,19 @@ def run_ours(args):
         f64_times.append(e0.elapsed_time(e1) / 1000.0)
     f64_s = statistics.mean(f64_times)
 
+    # ---- the same solve with every inner precision (one timed solve each)
+    by_inner = {}
+    for name, prec in (("f32", wdp.F32), ("q16", wdp.Q16), ("h16n", wdp.H16N), ("b16n", wdp.B16N)):
+        solve(prec)
+        flush.add_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        ri = solve(prec)
+        e1.record(s)
+        e1.synchronize()
+        by_inner[name] = {"ms": round(e0.elapsed_time(e1), 3), "iters": ri.iters, "updates": ri.reliable_updates,
+                          "true_rel_residual": ri.true_rel_residual}
+
     # ---- end to end through wd_solve with pinned host buffers
     bh = torch.from_numpy(b.view(np.float64).reshape(-1)).pin_memory()
     xh = torch.empty_like(bh).pin_memory()
@@ -291,17 +316,32 @@ def run_ours(args):
         assert r.status == 0
     e2e_value = ws * len(e2e_t) / max_over_ranks(ws, sum(e2e_t))
 
-    # ---- roofline of the dominant kernel: the inner-precision dslash on this
-    # lattice, same launch configuration as inside the solve, L2 flushed
-    t_ds = time_dslash(wd, torch, inner, 50, flush=flush)
+    # ---- rooflines.  The dominant kernel of the step is the FP64 dslash of the
+    # reliable updates (about 60% of the solve by the host-loop launch list),
+    # bound by the FP64 pipe: achieved = 1320 flops/site x Vh / launch time.
+    # The inner-precision dslash (the "dslash GB/s" of the metric) is bound by
+    # HBM: achieved = algorithmic bytes/site x Vh / launch time.  Both timed with
+    # CUDA events on the library's stream, same lattice and launch
+    # configuration as inside the solve, L2 flushed between launches.
     vh = V // 2
-    bytes_launch = BYTES_PER_SITE[inner] * vh
+    t64 = time_dslash(wd, torch, wdp.F64, 20, flush=flush)
+    f64_tflops = FLOPS_PER_SITE * vh / t64 / 1e12
+    traffic = NCU_TRAFFIC_BYTES.get(("f64", args.recon, "x".join(map(str, dims))))
+    roofline = {"bound": "alu", "achieved": round(f64_tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(f64_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "algorithmic_bytes": (8 * (16 * args.recon // 2) + 384) * vh, "peak_source": "measured FP64 FMA",
+                "kernel": f"dslash f64 {args.recon}-real (reliable update), {dims[0]}^3x{dims[3]}, {vh} sites/launch, "
+                          f"1320 flops/site", "us_per_launch": round(t64 * 1e6, 2)}
+    t_ds = time_dslash(wd, torch, inner, 50, flush=flush)
     hbm, src = peaks()
-    achieved = bytes_launch / t_ds / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-                "kernel": f"dslash {args.inner} 12-real, {dims[0]}^3x{dims[3]}, {vh} sites/launch, "
-                          f"{BYTES_PER_SITE[inner]} B/site algorithmic", "us_per_launch": round(t_ds * 1e6, 2)}
+    achieved = BYTES_PER_SITE[inner] * vh / t_ds / 1e9
+    dslash_roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(achieved / hbm, 4),
+                       "traffic": NCU_TRAFFIC_BYTES.get((args.inner, 12, "x".join(map(str, dims)))),
+                       "peak_source": src,
+                       "kernel": f"dslash {args.inner} 12-real (inner iteration), {dims[0]}^3x{dims[3]}, {vh} "
+                                 f"sites/launch, {BYTES_PER_SITE[inner]} B/site algorithmic",
+                       "us_per_launch": round(t_ds * 1e6, 2)}
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1000 * t_total / args.steps, 3), "higher_is_better": True,
@@ -315,9 +355,10 @@ def run_ours(args):
             "fp64_solve": {"ms_per_solve": round(1000 * f64_s, 3), "iters": f64_info.iters,
                            "true_rel_residual": f64_info.true_rel_residual},
             "speedup_vs_fp64": round(f64_s / (t_total / args.steps), 3),
+            "solve_by_inner_precision": by_inner,
             "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": V * 24 * 8,
                     "d2h_bytes_per_step": V * 24 * 8},
-            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+            "gpu_launches": launches, "roofline": roofline, "dslash_roofline": dslash_roofline, "clocks": clocks}
 
     # ---- dslash bandwidth sweep on the large lattice (inputs >> L2)
     if args.sweep and rank == 0:
@@ -444,7 +485,57 @@ def run_batch(args):
         assert r1.status == 0
         t_single += e0.elapsed_time(e1) / 1000.0
     t_single *= n / len(sample)
+    # the multi-RHS dslash against n single-RHS launches, inner precision
+    del fx, fx1
+    fin = wd.new_field(inner, n)
+    fin.zero_()
+    fout = wd.new_field(inner, n)
+    fbi = wd.field_bytes(inner)
+    ds = {}
+    for label in ("batched", "single"):
+        for rep in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            if label == "batched":
+                wd.dslash_batch(fout, fin, n, wdp.EVEN, False, inner)
+            else:
+                for q in range(n):
+                    wd.dslash(fout[q * fbi:(q + 1) * fbi], fin[q * fbi:(q + 1) * fbi], wdp.EVEN, False, inner)
+            e1.record(s)
+            e1.synchronize()
+            if rep:
+                ds.setdefault(label, []).append(e0.elapsed_time(e1) / 1000.0)
+    vh = li.volume(dims) // 2
+    t_b, t_s = statistics.mean(ds["batched"]), statistics.mean(ds["single"])
+    mrhs = {"batched_us": round(1e6 * t_b, 1), "single_x_n_us": round(1e6 * t_s, 1),
+            "batched_GB_per_s_algorithmic": round((8 * 24 + 2 * 52 * n) * vh / t_b / 1e9, 1)}
+    # the FP64 (reliable-update) dslash, batched against single launches
+    del fin, fout
+    n64 = 16
+    f64in = wd.new_field(wdp.F64, n64)
+    f64in.zero_()
+    f64out = wd.new_field(wdp.F64, n64)
+    fb64 = wd.field_bytes(wdp.F64)
+    d64 = {}
+    for label in ("batched", "single"):
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            if label == "batched":
+                wd.dslash_batch(f64out, f64in, n64, wdp.EVEN, False, wdp.F64)
+            else:
+                for q in range(n64):
+                    wd.dslash(f64out[q * fb64:(q + 1) * fb64], f64in[q * fb64:(q + 1) * fb64], wdp.EVEN, False,
+                              wdp.F64)
+            e1.record(s)
+            e1.synchronize()
+            if rep:
+                d64.setdefault(label, []).append(e0.elapsed_time(e1) / 1000.0)
+    mrhs["f64_batched16_us"] = round(1e6 * statistics.mean(d64["batched"]), 1)
+    mrhs["f64_single_x16_us"] = round(1e6 * statistics.mean(d64["single"]), 1)
+    del f64in, f64out
     print(json.dumps({"batch": "32x32x32x64, 12 point sources x 4 kappa", "n_systems": n, "inner": args.inner,
+                      "mrhs_dslash": mrhs,
                       "fp64_link_reals": args.recon, "s_per_batched_solve": round(t_batch, 4),
                       "systems_per_s": round(n / t_batch, 3), "s_first_call_incl_tuning": round(first_s, 3),
                       "s_one_at_a_time_est": round(t_single, 4), "batch_speedup": round(t_single / t_batch, 3),

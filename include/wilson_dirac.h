@@ -139,6 +139,11 @@ typedef struct {
   int inner_precision; /* wd_prec of the Krylov iteration; WD_F64 = pure FP64      */
   int use_graph;       /* 1: whole solve loop runs as one CUDA graph with device-side
                           conditional nodes; 0: host-driven loop                   */
+  int restart;         /* 0: reliable updates (Alg. 2).  1: defect correction
+                          (Alg. 1): each inner solve runs to eps_in = delta
+                          relative to its starting residual, then x += p,
+                          r = b - A x in FP64 and the Krylov iteration restarts
+                          (not for batched solves; needs a lower inner precision) */
 } wd_solve_params;
 
 typedef struct {

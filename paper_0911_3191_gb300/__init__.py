@@ -41,7 +41,8 @@ class WDError(RuntimeError):
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("solver", ctypes.c_int), ("inner_precision", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("inner_precision", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -227,12 +228,13 @@ class WilsonDirac:
         return r.value
 
     @staticmethod
-    def _params(tol, delta, max_iter, solver, inner_precision, use_graph):
+    def _params(tol, delta, max_iter, solver, inner_precision, use_graph, restart=False):
         return SolveParams(float(tol), float(delta), int(max_iter), int(solver), int(inner_precision),
-                           int(use_graph))
+                           int(use_graph), int(bool(restart)))
 
-    def _solve(self, fn, x, b, kappa, tol, delta, max_iter, solver, inner_precision, use_graph, check):
-        p = self._params(tol, delta, max_iter, solver, inner_precision, use_graph)
+    def _solve(self, fn, x, b, kappa, tol, delta, max_iter, solver, inner_precision, use_graph, check,
+               restart=False):
+        p = self._params(tol, delta, max_iter, solver, inner_precision, use_graph, restart)
         info = SolveInfo()
         st = fn(self.ctx, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), ctypes.byref(info))
         if check and st not in (0,):
@@ -244,16 +246,17 @@ class WilsonDirac:
                            int(info.kernel_launches))
 
     def solve(self, x, b, kappa, tol=1e-12, delta=0.1, max_iter=20000, solver=BICGSTAB, inner_precision=F64,
-              use_graph=True, check=True) -> SolveResult:
-        """x, b: (V, 4, 3) complex128 host arrays (pinned torch tensors also work)."""
+              use_graph=True, check=True, restart=False) -> SolveResult:
+        """x, b: (V, 4, 3) complex128 host arrays (pinned torch tensors also work).
+        restart=True: defect correction (Alg. 1) with eps_in = delta."""
         return self._solve(self.lib.wd_solve, x, b, kappa, tol, delta, max_iter, solver, inner_precision,
-                           use_graph, check)
+                           use_graph, check, restart)
 
     def solve_device(self, x, b, kappa, tol=1e-12, delta=0.1, max_iter=20000, solver=BICGSTAB,
-                     inner_precision=F64, use_graph=True, check=True) -> SolveResult:
+                     inner_precision=F64, use_graph=True, check=True, restart=False) -> SolveResult:
         """x, b: device FP64 full fields (``new_field(F64, 2)``)."""
         return self._solve(self.lib.wd_solve_device, x, b, kappa, tol, delta, max_iter, solver, inner_precision,
-                           use_graph, check)
+                           use_graph, check, restart)
 
     def dslash_batch(self, out, inp, nrhs: int, out_parity: int, dagger: bool, prec: int):
         """out_r = D in_r for nrhs single-parity fields stored back to back."""

@@ -38,7 +38,7 @@ __global__ void loop_control_kernel(SolverCtl* ctl) {
 
 __global__ void init_ctl_kernel(SolverCtl* ctl, double tol, double delta, int max_iter, double kappa,
                                 const double* bnorm2, int in_graph, unsigned long long h_update,
-                                unsigned long long h_loop) {
+                                unsigned long long h_loop, int restart) {
   SolverCtl c;
   memset(&c, 0, sizeof(c));
   const double one = 1.0;
@@ -51,6 +51,7 @@ __global__ void init_ctl_kernel(SolverCtl* ctl, double tol, double delta, int ma
   c.max_iter = max_iter;
   c.status = WD_OK;
   c.in_graph = in_graph;
+  c.restart = restart;
   c.h_update = h_update;
   c.h_loop = h_loop;
   *ctl = c;
@@ -394,9 +395,11 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
                        wd_solve_info* info) {
   Ctx& c = ctx->c;
   const auto t0 = std::chrono::steady_clock::now();
-  wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_F64, 1};
+  wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_F64, 1, 0};
   if (prm) p = *prm;
   if (!valid_prec(p.inner_precision)) return set_err(ctx, WD_ERR_INVALID_ARG, "bad inner_precision");
+  if (p.restart && p.inner_precision == WD_F64)
+    return set_err(ctx, WD_ERR_INVALID_ARG, "defect correction needs a lower inner precision");
   if (p.solver != WD_BICGSTAB && p.solver != WD_CGNR) return set_err(ctx, WD_ERR_INVALID_ARG, "bad solver");
   if (!(p.tol > 0.0) || p.max_iter <= 0) return set_err(ctx, WD_ERR_INVALID_ARG, "bad tol or max_iter");
   if (p.inner_precision == WD_F64) p.delta = 0.0;  // pure FP64: update only to confirm convergence
@@ -433,7 +436,7 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     hl = c.graph_hl;
   }
   init_ctl_kernel<<<1, 1, 0, s>>>(sb.ctl, p.tol, p.delta, p.max_iter, kappa, c.scalars, p.use_graph ? 1 : 0, hu,
-                                  hl);
+                                  hl, p.restart ? 1 : 0);
   if (p.solver == WD_BICGSTAB) oin->bicg_setup(c, sb, s);
   else oin->cg_setup(c, sb, s);
   WD_CK_LAUNCH(ctx, "solver setup");
@@ -510,7 +513,7 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     // per reliable update: BiCGstab 3 (CG 5); end: x_o and two residual dslash
     const long long setup = 3 + 1 + 1 + 1 + 4;
     const long long per_it = (p.solver == WD_BICGSTAB ? 7 : 5) + (p.use_graph ? 1 : 0);
-    const long long per_up = (p.solver == WD_BICGSTAB) ? 3 : 5;
+    const long long per_up = (p.solver == WD_BICGSTAB) ? 4 : 5;
     info->kernel_launches = setup + (long long)hc.iter * per_it + (long long)hc.updates * per_up + 3;
   }
   if (result != WD_OK) {

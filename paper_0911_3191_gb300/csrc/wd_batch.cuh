@@ -31,6 +31,8 @@ struct BatchCtl {
   int step_loops;  // WHILE-body executions since the host last launched the loop
   int step_limit;  // pause (return to the host) after this many, for serving
   unsigned long long h_update, h_loop;
+  int nupd;           // systems due for a reliable update this iteration
+  int upd_list[256];  // their indices, ascending
 };
 
 struct BatchArgs {
@@ -38,6 +40,7 @@ struct BatchArgs {
   const SolverCtl* ctl;  // nullptr: every right-hand side active
   int mode;              // 0: active unless done; 1: active when an update is due
   double* partials;      // [(r * NRED + k) * nblocks + block]
+  const BatchCtl* bc;    // mode 1: the compacted list of systems due for an update
 };
 
 __device__ __forceinline__ bool rhs_active(const BatchArgs& a, int r) {
@@ -87,6 +90,30 @@ __device__ __forceinline__ void hop_tile(const In& in, const R* lk, int sx, int 
   }
 }
 
+// temporal hop from the tile: half-spinor load, diagonal projector
+template <bool FWD, bool DAGGER, typename R, class In>
+__device__ __forceinline__ void hop_tile_t(const In& in, const R* lk, int sx, int h_nbr, bool flip, R (&acc)[24]) {
+  constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  constexpr bool upper = (S == +1);
+  constexpr int which = 6 + (FWD ? 0 : 1);
+  R hs[12];
+  R w = 1;
+  if constexpr (In::kScaled) {
+    float f[12];
+    w = in.load_raw_half(h_nbr, upper, f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) hs[k] = f[k];
+  } else {
+    in.load_half(h_nbr, upper, hs);
+  }
+  R u[18];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) u[k] = lk[(which * 18 + k) * 32 + sx];
+  R gs[12];
+  su3_mul<!FWD>(u, hs, gs);
+  accumulate_temporal<FWD, upper>(gs, acc, flip ? -(R)2 * w : (R)2 * w);
+}
+
 template <bool DAGGER, typename R, class In>
 __device__ __forceinline__ void dslash_site_tile(const In& in, const R* lk, int sx, const int (&nb)[8], bool top,
                                                  bool bot, R (&acc)[24]) {
@@ -98,8 +125,8 @@ __device__ __forceinline__ void dslash_site_tile(const In& in, const R* lk, int 
   hop_tile<1, false, DAGGER>(in, lk, sx, nb[3], false, acc);
   hop_tile<2, true, DAGGER>(in, lk, sx, nb[4], false, acc);
   hop_tile<2, false, DAGGER>(in, lk, sx, nb[5], false, acc);
-  hop_tile<3, true, DAGGER>(in, lk, sx, nb[6], top, acc);
-  hop_tile<3, false, DAGGER>(in, lk, sx, nb[7], bot, acc);
+  hop_tile_t<true, DAGGER>(in, lk, sx, nb[6], top, acc);
+  hop_tile_t<false, DAGGER>(in, lk, sx, nb[7], bot, acc);
 }
 
 template <typename R>
@@ -149,8 +176,10 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
       top = g.tbc_anti && (t == g.T - 1);
       bot = g.tbc_anti && (t == 0);
     }
-    for (int r0 = 0; r0 < ba.nrhs; r0 += TR) {
-      const int r = r0 + threadIdx.y;
+    const int nwork = (ba.mode == 1 && ba.bc) ? *(const volatile int*)&ba.bc->nupd : ba.nrhs;
+    for (int r0 = 0; r0 < nwork; r0 += TR) {
+      const int i = r0 + threadIdx.y;
+      const int r = (ba.mode == 1 && ba.bc) ? (i < nwork ? ba.bc->upd_list[i] : ba.nrhs) : i;
       double red[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) red[k] = 0.0;
@@ -226,10 +255,11 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(BatchArgs ba, int n
     int any = 0;
     for (int q = 0; q < ba.nrhs; ++q) {
       const volatile SolverCtl* c = ba.ctl + q;
-      if (!c->done && c->do_update) any = 1;
+      if (!c->done && c->do_update) bc->upd_list[any++] = q;
     }
-    bc->any_update = any;
-    if (bc->in_graph) cudaGraphSetConditional((cudaGraphConditionalHandle)bc->h_update, (unsigned)any);
+    bc->nupd = any;
+    bc->any_update = any > 0;
+    if (bc->in_graph) cudaGraphSetConditional((cudaGraphConditionalHandle)bc->h_update, any > 0 ? 1u : 0u);
   }
 }
 
@@ -246,26 +276,35 @@ __global__ void batch_init_kernel(SolverCtl* ctl, BatchCtl* bc, int nrhs, double
 // ------------------------------------------------------------ launchers
 struct BatchLaunch {
   int nrhs;
-  int tr;       // right-hand sides per chunk (1, 2, 4 or 8)
-  int grid;     // multi-RHS dslash blocks
+  int tr;       // right-hand sides per chunk (1, 2, 4 or 8), inner precision
+  int grid;     // multi-RHS dslash blocks, inner precision
   int blas_gx;  // site-kernel blocks per right-hand side
+  int tr64 = 8;      // the FP64 (reliable-update) dslash: bound by the FP64 pipe,
+  int grid64 = 0;    // it wants many warps; 0 = same grid as the inner precision
 };
+
+template <typename R>
+inline int mrhs_grid(const BatchLaunch& bl) {
+  return (sizeof(R) == 8 && bl.grid64 > 0) ? bl.grid64 : bl.grid;
+}
 
 template <typename R, class In, class G, class Epi>
 void launch_dslash_mrhs(const Geom& g, const BatchLaunch& bl, const In& in, const G& gauge, int parity, int dagger,
                         const Epi& epi, const BatchArgs& ba, cudaStream_t s) {
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   const size_t smem = tile_link_bytes<R>() + (size_t)bl.nrhs * NR * sizeof(double);
+  const int tr = (sizeof(R) == 8) ? bl.tr64 : bl.tr;
+  const int grid = mrhs_grid<R>(bl);
 #define WD_MRHS_CASE(TRV)                                                                                   \
   case TRV:                                                                                                 \
     if (dagger)                                                                                             \
-      dslash_mrhs_kernel<true, R, In, G, Epi, TRV><<<bl.grid, dim3(32, TRV), smem, s>>>(g, in, gauge, parity, \
-                                                                                        epi, ba);           \
+      dslash_mrhs_kernel<true, R, In, G, Epi, TRV><<<grid, dim3(32, TRV), smem, s>>>(g, in, gauge, parity,    \
+                                                                                     epi, ba);              \
     else                                                                                                    \
-      dslash_mrhs_kernel<false, R, In, G, Epi, TRV><<<bl.grid, dim3(32, TRV), smem, s>>>(g, in, gauge,       \
-                                                                                         parity, epi, ba);  \
+      dslash_mrhs_kernel<false, R, In, G, Epi, TRV><<<grid, dim3(32, TRV), smem, s>>>(g, in, gauge, parity,   \
+                                                                                      epi, ba);             \
     break;
-  switch (bl.tr) {
+  switch (tr) {
     WD_MRHS_CASE(1)
     WD_MRHS_CASE(2)
     WD_MRHS_CASE(4)
@@ -357,7 +396,7 @@ struct ImplBatch {
   // reliable update for the systems that asked for one (mode 1)
   static void update(const Ctx& c, const BatchLaunch& bl, BatchBufs& b, cudaStream_t s) {
     const Geom& g = c.g;
-    BatchArgs ba{bl.nrhs, b.ctl, 1, b.partials};
+    BatchArgs ba{bl.nrhs, b.ctl, 1, b.partials, b.bc};
     const Coef nk2{0.0, &b.ctl->neg_kappa2, (long)(sizeof(SolverCtl) / sizeof(double))};
     launch_sites_batch(g, bl, OpAccumulate<S>{v64(b.xe, g, fb64(g)), v(b.x_hat, g)}, ba, s);
     EpiStore<SpinorF64> e0{v64(b.tmp64, g, fb64(g))};
@@ -365,7 +404,7 @@ struct ImplBatch {
     EpiRelupBicg<S, S, FinRelupBicg> e1{v64(b.b_hat, g, fb64(g)), v64(b.xe, g, fb64(g)), v(b.r_hat, g),
                                         v(b.r_tilde, g), nk2, c.red, FinRelupBicg{b.ctl}};
     launch_dslash_mrhs<double>(g, bl, v64(b.tmp64, g, fb64(g)), T64::gauge(c), 0, 0, e1, ba, s);
-    launch_finalize<4>(bl, ba, bl.grid, FinRelupBicg{b.ctl}, b.bc, 3, 0, s);
+    launch_finalize<4>(bl, ba, mrhs_grid<double>(bl), FinRelupBicg{b.ctl}, b.bc, 3, 0, s);
   }
 };
 

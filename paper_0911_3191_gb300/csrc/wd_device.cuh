@@ -114,6 +114,17 @@ struct SpinorF64 {
       v[2 * c + 1] = (R)d.y;
     }
   }
+  // spins 0,1 (upper) or 2,3 (lower): 12 reals
+  template <typename R>
+  __device__ __forceinline__ void load_half(int h, bool upper, R (&v)[12]) const {
+    const int c0 = upper ? 0 : 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double2 d = __ldg(p + (size_t)(c0 + c) * stride + h);
+      v[2 * c] = (R)d.x;
+      v[2 * c + 1] = (R)d.y;
+    }
+  }
   template <typename R>
   __device__ __forceinline__ void store(int h, const R (&v)[24]) const {
 #pragma unroll
@@ -143,6 +154,18 @@ struct SpinorF32 {
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       float4 d = __ldg(p + (size_t)c * stride + h);
+      v[4 * c] = (R)d.x;
+      v[4 * c + 1] = (R)d.y;
+      v[4 * c + 2] = (R)d.z;
+      v[4 * c + 3] = (R)d.w;
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_half(int h, bool upper, R (&v)[12]) const {
+    const int c0 = upper ? 0 : 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4 d = __ldg(p + (size_t)(c0 + c) * stride + h);
       v[4 * c] = (R)d.x;
       v[4 * c + 1] = (R)d.y;
       v[4 * c + 2] = (R)d.z;
@@ -237,6 +260,29 @@ struct Spinor16 {
     if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
     else return n;
   }
+  // spins 0,1 (values 0..11: chunk 0 and the first half of chunk 1) or
+  // spins 2,3 (values 12..23: the second half of chunk 1 and chunk 2)
+  __device__ __forceinline__ float load_raw_half(int h, bool upper, float (&v)[12]) const {
+    uint32_t w[6];
+    if (upper) {
+      const uint4 a = __ldg(p + h);
+      const uint2 b = __ldg(reinterpret_cast<const uint2*>(p + (size_t)stride + h));
+      w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y;
+    } else {
+      const uint2 a = __ldg(reinterpret_cast<const uint2*>(p + (size_t)stride + h) + 1);
+      const uint4 b = __ldg(p + (size_t)2 * stride + h);
+      w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = b.z; w[5] = b.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float2 f = pair(w[j]);
+      v[2 * j] = f.x;
+      v[2 * j + 1] = f.y;
+    }
+    float n = __ldg(norm + h);
+    if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
+    else return n;
+  }
   template <typename R>
   __device__ __forceinline__ void load(int h, R (&v)[24]) const {
     float f[24];
@@ -312,8 +358,14 @@ __device__ __forceinline__ void reconstruct_row3(R (&u)[18]) {
     const int j = (i + 1) % 3, k = (i + 2) % 3;
     R ajr = u[2 * j], aji = u[2 * j + 1], akr = u[2 * k], aki = u[2 * k + 1];
     R bjr = u[6 + 2 * j], bji = u[6 + 2 * j + 1], bkr = u[6 + 2 * k], bki = u[6 + 2 * k + 1];
-    R re = (ajr * bkr - aji * bki) - (akr * bjr - aki * bji);
-    R im = (ajr * bki + aji * bkr) - (akr * bji + aki * bjr);
+    R re = ajr * bkr;
+    re -= aji * bki;
+    re -= akr * bjr;
+    re += aki * bji;
+    R im = ajr * bki;
+    im += aji * bkr;
+    im -= akr * bji;
+    im -= aki * bjr;
     u[12 + 2 * i] = re;
     u[12 + 2 * i + 1] = -im;
   }
@@ -410,16 +462,24 @@ using GaugeH16 = Gauge16<Fmt16::H16>;
 using GaugeB16 = Gauge16<Fmt16::B16>;
 
 // ----------------------------------------------- spin projection (App. B)
-// Half spinor h[(s * 3 + c) * 2 + reim], s = 0, 1.  For the projector
-// P = 1 + S gamma_mu in the DeGrand-Rossi basis the two upper rows of P psi
-// determine the lower two; project() forms the upper rows, reconstruct()
-// adds the full four-spinor P psi' given the transformed upper rows psi'.
-//   mu = x: h0 = p0 + S i p3, h1 = p1 + S i p2;  lower = (-S i h1, -S i h0)
-//   mu = y: h0 = p0 - S p3,   h1 = p1 + S p2;    lower = ( S h1,   -S h0)
-//   mu = z: h0 = p0 + S i p2, h1 = p1 - S i p3;  lower = (-S i h0,  S i h1)
-//   mu = t: h0 = p0 + S p2,   h1 = p1 + S p3;    lower = ( S h0,    S h1)
-template <int MU, int S, typename R>
+// The kernels work in the "non-relativistic" (UKQCD) basis of App. B, in
+// which gamma_4 = diag(1,1,-1,-1): a temporal hop needs only two spin
+// components of the neighbour (P^{+4} = diag(2,2,0,0), P^{-4} = diag(0,0,2,2)),
+// so it loads half a spinor.  Fields cross the host boundary in the
+// DeGrand-Rossi basis; import/export apply the basis change (psi_UK = S
+// psi_DR, see OpImport).  In this basis gamma_1 and gamma_3 are those of the
+// DeGrand-Rossi set and gamma_2 has the opposite sign.
+// Half spinor h[(s * 3 + c) * 2 + reim], s = 0, 1.  For the spatial
+// projectors P = 1 + S gamma_mu the two upper rows of P psi determine the
+// lower two; project() forms the upper rows, reconstruct() adds the full
+// four-spinor given the transformed upper rows g (here S2 = -S for y):
+//   mu = x: h0 = p0 + S i p3,  h1 = p1 + S i p2;   lower = (-S i g1, -S i g0)
+//   mu = y: h0 = p0 - S2 p3,   h1 = p1 + S2 p2;    lower = ( S2 g1,  -S2 g0)
+//   mu = z: h0 = p0 + S i p2,  h1 = p1 - S i p3;   lower = (-S i g0,  S i g1)
+template <int MU, int S_, typename R>
 __device__ __forceinline__ void project(const R (&p)[24], R (&h)[12]) {
+  static_assert(MU < 3, "temporal hops are diagonal in this basis");
+  constexpr int S = (MU == 1) ? -S_ : S_;
   constexpr R s = (R)S;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -434,20 +494,19 @@ __device__ __forceinline__ void project(const R (&p)[24], R (&h)[12]) {
     } else if constexpr (MU == 1) {
       h0r = p0r - s * p3r; h0i = p0i - s * p3i;
       h1r = p1r + s * p2r; h1i = p1i + s * p2i;
-    } else if constexpr (MU == 2) {
+    } else {
       h0r = p0r - s * p2i; h0i = p0i + s * p2r;
       h1r = p1r + s * p3i; h1i = p1i - s * p3r;
-    } else {
-      h0r = p0r + s * p2r; h0i = p0i + s * p2i;
-      h1r = p1r + s * p3r; h1i = p1i + s * p3i;
     }
     h[c * 2] = h0r; h[c * 2 + 1] = h0i;
     h[(3 + c) * 2] = h1r; h[(3 + c) * 2 + 1] = h1i;
   }
 }
 
-template <int MU, int S, typename R>
+template <int MU, int S_, typename R>
 __device__ __forceinline__ void reconstruct(const R (&g)[12], R (&a)[24]) {
+  static_assert(MU < 3, "temporal hops are diagonal in this basis");
+  constexpr int S = (MU == 1) ? -S_ : S_;
   constexpr R s = (R)S;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -461,20 +520,19 @@ __device__ __forceinline__ void reconstruct(const R (&g)[12], R (&a)[24]) {
     } else if constexpr (MU == 1) {  // lower = (S g1, -S g0)
       a[(6 + c) * 2] += s * g1r; a[(6 + c) * 2 + 1] += s * g1i;
       a[(9 + c) * 2] -= s * g0r; a[(9 + c) * 2 + 1] -= s * g0i;
-    } else if constexpr (MU == 2) {  // lower = (-S i g0, S i g1)
+    } else {  // mu = z: lower = (-S i g0, S i g1)
       a[(6 + c) * 2] += s * g0i; a[(6 + c) * 2 + 1] -= s * g0r;
       a[(9 + c) * 2] -= s * g1i; a[(9 + c) * 2 + 1] += s * g1r;
-    } else {  // lower = (S g0, S g1)
-      a[(6 + c) * 2] += s * g0r; a[(6 + c) * 2 + 1] += s * g0i;
-      a[(9 + c) * 2] += s * g1r; a[(9 + c) * 2 + 1] += s * g1i;
     }
   }
 }
 
 // reconstruct() with every term scaled by w (the decode scale of a 16-bit
 // neighbour and link, times a boundary sign): a += w P psi' in one FFMA each
-template <int MU, int S, typename R>
+template <int MU, int S_, typename R>
 __device__ __forceinline__ void reconstruct_scaled(const R (&g)[12], R (&a)[24], R w) {
+  static_assert(MU < 3, "temporal hops are diagonal in this basis");
+  constexpr int S = (MU == 1) ? -S_ : S_;
   const R ws = w * (R)S;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -488,12 +546,9 @@ __device__ __forceinline__ void reconstruct_scaled(const R (&g)[12], R (&a)[24],
     } else if constexpr (MU == 1) {
       a[(6 + c) * 2] += ws * g1r; a[(6 + c) * 2 + 1] += ws * g1i;
       a[(9 + c) * 2] -= ws * g0r; a[(9 + c) * 2 + 1] -= ws * g0i;
-    } else if constexpr (MU == 2) {
+    } else {
       a[(6 + c) * 2] += ws * g0i; a[(6 + c) * 2 + 1] -= ws * g0r;
       a[(9 + c) * 2] -= ws * g1i; a[(9 + c) * 2 + 1] += ws * g1r;
-    } else {
-      a[(6 + c) * 2] += ws * g0r; a[(6 + c) * 2 + 1] += ws * g0i;
-      a[(9 + c) * 2] += ws * g1r; a[(9 + c) * 2 + 1] += ws * g1i;
     }
   }
 }
@@ -505,14 +560,25 @@ __device__ __forceinline__ void su3_mul(const R (&u)[18], const R (&h)[12], R (&
   for (int s = 0; s < 2; ++s) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
+      // one FMA per real product: each accumulation is its own statement
+      // (an expression "re += a*b - c*d" costs a multiply, an FMA and an add)
       R re = 0, im = 0;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int e = DAG ? (j * 3 + i) : (i * 3 + j);
-        const R ur = u[2 * e], ui = DAG ? -u[2 * e + 1] : u[2 * e + 1];
+        const R ur = u[2 * e], ui = u[2 * e + 1];
         const R hr = h[(s * 3 + j) * 2], hi = h[(s * 3 + j) * 2 + 1];
-        re += ur * hr - ui * hi;
-        im += ur * hi + ui * hr;
+        if constexpr (DAG) {  // conj(U_ji) h_j
+          re += ur * hr;
+          re += ui * hi;
+          im += ur * hi;
+          im -= ui * hr;
+        } else {  // U_ij h_j
+          re += ur * hr;
+          re -= ui * hi;
+          im += ur * hi;
+          im += ui * hr;
+        }
       }
       g[(s * 3 + i) * 2] = re;
       g[(s * 3 + i) * 2 + 1] = im;
@@ -522,6 +588,42 @@ __device__ __forceinline__ void su3_mul(const R (&u)[18], const R (&h)[12], R (&
 
 // One hop of the stencil: acc += P^{S mu} U psi(neighbour), where
 // S = -1 forward / +1 backward for D, exchanged for D^dag (Sec. 3, eq. for M).
+// Temporal hop: P^{S 4} = 2 x (projector on spins 0,1 for S = +1, on 2,3 for
+// S = -1); acc on those spins += 2 w (U or U^dag) psi_half
+template <bool FWD, bool UPPER, typename R>
+__device__ __forceinline__ void accumulate_temporal(const R (&g)[12], R (&a)[24], R w2) {
+  constexpr int o = UPPER ? 0 : 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a[o + k] += w2 * g[k];
+}
+
+template <bool FWD, bool DAGGER, typename R, class In, class G>
+__device__ __forceinline__ void hop_t(const In& in, const G& gauge, int parity, int h_link, int h_nbr, bool flip,
+                                      R (&acc)[24]) {
+  constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  constexpr bool upper = (S == +1);
+  R hs[12];
+  R w = 1;
+  if constexpr (In::kScaled) {
+    float f[12];
+    w = in.load_raw_half(h_nbr, upper, f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) hs[k] = f[k];
+  } else {
+    in.load_half(h_nbr, upper, hs);
+  }
+  R u[18];
+  if constexpr (G::kScaled) {
+    gauge.load_raw(FWD ? parity : 1 - parity, 3, h_link, u);
+    w *= (R)G::kScale;
+  } else {
+    gauge.load(FWD ? parity : 1 - parity, 3, h_link, u);
+  }
+  R gs[12];
+  su3_mul<!FWD>(u, hs, gs);
+  accumulate_temporal<FWD, upper>(gs, acc, flip ? -(R)2 * w : (R)2 * w);
+}
+
 template <int MU, bool FWD, bool DAGGER, typename R, class In, class G>
 __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, int h_link, int h_nbr, bool flip,
                                     R (&acc)[24]) {
@@ -587,8 +689,8 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const In& in, const G
     const bool top = (t == g.T - 1), bot = (t == 0);
     const int np = top ? h - g.wt : h + g.XhYZ;
     const int nm = bot ? h + g.wt : h - g.XhYZ;
-    hop<3, true, DAGGER>(in, gauge, parity, h, np, top && g.tbc_anti, acc);
-    hop<3, false, DAGGER>(in, gauge, parity, nm, nm, bot && g.tbc_anti, acc);
+    hop_t<true, DAGGER>(in, gauge, parity, h, np, top && g.tbc_anti, acc);
+    hop_t<false, DAGGER>(in, gauge, parity, nm, nm, bot && g.tbc_anti, acc);
   }
 }
 

@@ -35,6 +35,7 @@ struct SolverCtl {
   int do_update;     // 1 when this iteration ends with a reliable update
   int forced;        // the update was forced by apparent convergence or max_iter
   int in_graph;      // 1: running inside the solver graph (set the conditionals)
+  int restart;       // 1: defect correction (Alg. 1): every update restarts the Krylov space
   int loops;         // WHILE-body executions, counted by the loop control kernel
   int pad;
   unsigned long long h_update;  // graph conditional handles (used when in_graph)

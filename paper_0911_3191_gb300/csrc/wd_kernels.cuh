@@ -81,7 +81,9 @@ __device__ __forceinline__ void decide_update(SolverCtl* ctl, double rr, double 
   const bool rel = r < ctl->delta * ctl->maxr;
   const int upd = (conv || maxed || rel) ? 1 : 0;
   ctl->forced = (conv || maxed) ? 1 : 0;
-  if (!upd) ctl->maxr = fmax(ctl->maxr, r);
+  // Alg. 2 compares with the largest residual since the last update; defect
+  // correction (Alg. 1) solves to eps_in relative to the restart residual
+  if (!upd && !ctl->restart) ctl->maxr = fmax(ctl->maxr, r);
   ctl_set_update(ctl, upd);
 }
 
@@ -115,8 +117,16 @@ struct FinRelupBicg {
     ctl->r2_true = r2;
     ctl->rr = t[3];
     ctl->maxr = sqrt(t[3]);
-    ctl->rho = rho;
-    ctl->beta = cmul(cdiv(rho, ctl->rho_prev), cdiv(ctl->alpha, ctl->omega));
+    if (ctl->restart) {
+      // Alg. 1: a new inner solve from the new residual (r_tilde = r_hat,
+      // p = v = 0, set by OpRestart in the same update)
+      ctl->rho = make_double2(t[3], 0.0);
+      ctl->rho_prev = ctl->alpha = ctl->omega = make_double2(1.0, 0.0);
+      ctl->beta = make_double2(0.0, 0.0);
+    } else {
+      ctl->rho = rho;
+      ctl->beta = cmul(cdiv(rho, ctl->rho_prev), cdiv(ctl->alpha, ctl->omega));
+    }
     if (r2 <= ctl->stop2) { ctl->status = WD_OK; ctl->done = 1; }
     else if (ctl->iter >= ctl->max_iter) ctl_fail(ctl, WD_ERR_NOT_CONVERGED);
     else if (rho.x == 0.0 && rho.y == 0.0) ctl_fail(ctl, WD_ERR_BREAKDOWN);
@@ -188,7 +198,8 @@ struct FinRelupCgN {
     if (!isfinite(rr)) { ctl_fail(ctl, WD_ERR_NUMERIC); return; }
     ctl->rr = rr;
     ctl->maxr = sqrt(rr);
-    ctl->beta = make_double2(rr / ctl->rr_prev, 0.0);
+    // defect correction restarts CG from the new residual: p = r_hat
+    ctl->beta = ctl->restart ? make_double2(0.0, 0.0) : make_double2(rr / ctl->rr_prev, 0.0);
   }
 };
 
@@ -263,8 +274,10 @@ struct EpiXpayDot {
     R re = 0, im = 0;  // this site's 12 terms in the kernel's precision
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      re += wv[2 * k] * a[2 * k] + wv[2 * k + 1] * a[2 * k + 1];
-      im += wv[2 * k] * a[2 * k + 1] - wv[2 * k + 1] * a[2 * k];
+      re += wv[2 * k] * a[2 * k];
+      re += wv[2 * k + 1] * a[2 * k + 1];
+      im += wv[2 * k] * a[2 * k + 1];
+      im -= wv[2 * k + 1] * a[2 * k];
     }
     red[0] += (double)re;  // global sum in FP64
     red[1] += (double)im;
@@ -293,9 +306,12 @@ struct EpiXpayTS {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const R tr = a[2 * k], ti = a[2 * k + 1], sr = sv[2 * k], si = sv[2 * k + 1];
-      re += tr * sr + ti * si;
-      im += tr * si - ti * sr;
-      tt += tr * tr + ti * ti;
+      re += tr * sr;
+      re += ti * si;
+      im += tr * si;
+      im -= ti * sr;
+      tt += tr * tr;
+      tt += ti * ti;
     }
     red[0] += (double)re;
     red[1] += (double)im;
@@ -431,9 +447,12 @@ struct EpiRelupBicg {
     double re = 0.0, im = 0.0, m = 0.0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      re += wv[2 * k] * a[2 * k] + wv[2 * k + 1] * a[2 * k + 1];
-      im += wv[2 * k] * a[2 * k + 1] - wv[2 * k + 1] * a[2 * k];
-      m += a[2 * k] * a[2 * k] + a[2 * k + 1] * a[2 * k + 1];
+      re += wv[2 * k] * a[2 * k];
+      re += wv[2 * k + 1] * a[2 * k + 1];
+      im += wv[2 * k] * a[2 * k + 1];
+      im -= wv[2 * k + 1] * a[2 * k];
+      m += a[2 * k] * a[2 * k];
+      m += a[2 * k + 1] * a[2 * k + 1];
     }
     red[1] += re;
     red[2] += im;
@@ -485,8 +504,10 @@ __device__ __forceinline__ void cmac(R (&y)[24], double2 a, const R (&x)[24]) { 
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const R xr = x[2 * k], xi = x[2 * k + 1];
-    y[2 * k] += ar * xr - ai * xi;
-    y[2 * k + 1] += ar * xi + ai * xr;
+    y[2 * k] += ar * xr;
+    y[2 * k] -= ai * xi;
+    y[2 * k + 1] += ar * xi;
+    y[2 * k + 1] += ai * xr;
   }
 }
 
@@ -560,9 +581,12 @@ struct OpBicgFinal {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       const R a = sv[2 * k], b = sv[2 * k + 1], wr = wv[2 * k], wi = wv[2 * k + 1];
-      n += a * a + b * b;
-      re += wr * a + wi * b;
-      im += wr * b - wi * a;
+      n += a * a;
+      n += b * b;
+      re += wr * a;
+      re += wi * b;
+      im += wr * b;
+      im -= wi * a;
     }
     red[0] += (double)n;
     red[1] += (double)re;
@@ -607,6 +631,28 @@ struct OpAccumulate {
     }
     x.store(h, xv);
     xh.store(h, hv);
+  }
+};
+
+// defect correction only (ctl->restart): r_tilde = r_hat, p = v = 0
+template <class S>
+struct OpRestart {
+  static constexpr int NRED = 0;
+  S rt, rh, p, v;
+  const SolverCtl* ctl;
+  __device__ __forceinline__ OpRestart at(int q) const {
+    return OpRestart{rt.at(q), rh.at(q), p.at(q), v.at(q), ctl + q};
+  }
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    using R = typename S::real;
+    if (!ctl->restart) return;
+    R a[24];
+    rh.load(h, a);
+    rt.store(h, a);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) a[k] = 0;
+    p.store(h, a);
+    v.store(h, a);
   }
 };
 
@@ -682,6 +728,34 @@ struct OpZero {
   }
 };
 
+// App. B basis change, applied when a spinor crosses the host boundary:
+// psi_int = S psi_DR with the real orthogonal
+//   S = (1/sqrt 2) [[0,1,0,1], [-1,0,-1,0], [0,1,0,-1], [-1,0,1,0]],
+// for which S gamma_mu S^T is the gamma_mu of the UKQCD set printed in App. B
+// (gamma_4 diagonal).  Spinor index (spin * 3 + colour) * 2 + reim.
+__device__ __forceinline__ void to_internal_basis(const double (&d)[24], double (&v)[24]) {
+  constexpr double r = 0.70710678118654752440;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double p0 = d[k], p1 = d[6 + k], p2 = d[12 + k], p3 = d[18 + k];
+    v[k] = r * (p1 + p3);
+    v[6 + k] = -r * (p0 + p2);
+    v[12 + k] = r * (p1 - p3);
+    v[18 + k] = r * (p2 - p0);
+  }
+}
+__device__ __forceinline__ void to_host_basis(const double (&v)[24], double (&d)[24]) {
+  constexpr double r = 0.70710678118654752440;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double u0 = v[k], u1 = v[6 + k], u2 = v[12 + k], u3 = v[18 + k];
+    d[k] = -r * (u1 + u3);
+    d[6 + k] = r * (u0 + u2);
+    d[12 + k] = r * (u3 - u1);
+    d[18 + k] = r * (u0 - u2);
+  }
+}
+
 // host layout (lexicographic FP64, [site][spin][colour][re,im]) <-> field
 template <class S>
 struct OpImport {
@@ -694,14 +768,15 @@ struct OpImport {
     int x, y, z, t;
     site_coords(g, h, parity, x, y, z, t);
     const size_t s = (size_t)x + (size_t)g.X * (y + (size_t)g.Y * (z + (size_t)g.Z * t));
-    double v[24];
+    double d[24], v[24];
     const double2* src = reinterpret_cast<const double2*>(lex + 24 * s);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      double2 d = src[k];
-      v[2 * k] = d.x;
-      v[2 * k + 1] = d.y;
+      double2 e = src[k];
+      d[2 * k] = e.x;
+      d[2 * k + 1] = e.y;
     }
+    to_internal_basis(d, v);
     out.store(h, v);
   }
 };
@@ -720,9 +795,13 @@ struct OpExport {
     const size_t s = (size_t)x + (size_t)g.X * (y + (size_t)g.Y * (z + (size_t)g.Z * t));
     R v[24];
     in.load(h, v);
+    double w[24], d[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) w[k] = (double)v[k];
+    to_host_basis(w, d);
     double2* dst = reinterpret_cast<double2*>(lex + 24 * s);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+    for (int k = 0; k < 12; ++k) dst[k] = make_double2(d[2 * k], d[2 * k + 1]);
   }
 };
 
@@ -876,6 +955,9 @@ struct Impl {
                                          T::view(b.r_tilde, g), Coef{0.0, &b.ctl->neg_kappa2}, c.red,
                                          FinRelupBicg{b.ctl}};
     launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 0, e1, s);
+    launch_sites(c, g.Vh, OpRestart<S>{T::view(b.r_tilde, g), T::view(b.r_hat, g), T::view(b.p, g), T::view(b.v, g),
+                                       b.ctl},
+                 s);
   }
 
   // ---- CG on M_hat^dag M_hat (Sec. 5.1), inner precision P

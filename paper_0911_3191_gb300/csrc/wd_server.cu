@@ -59,7 +59,8 @@ struct Pool {
   std::deque<long long> queue;
   SolverCtl* hctl = nullptr;        // pinned mirror of the ctl array
   double* hscal = nullptr;          // pinned mirror of per-slot scalars
-  bool launched = false;
+  bool launched = false;            // a step of iterations is in flight
+  cudaEvent_t done_ev = nullptr;    // recorded after the step's iterations
 };
 
 }  // namespace
@@ -214,6 +215,8 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
   b.tmp = p; p += fin * cap;
   const int ntiles = (c.g.Vh + 31) / 32;
   pl.bl = BatchLaunch{cap, 4, std::min(c.num_sms * 4, ntiles), blas_gx_for(c, cap)};
+  pl.bl.tr64 = 8;
+  pl.bl.grid64 = std::min(c.num_sms * 4, ntiles);
   mark_free_kernel<<<(cap + 127) / 128, 128, 0, c.stream>>>(b.ctl, cap);
   WS_CK(sv, cudaGetLastError());
   if (sv->p.use_graph) {
@@ -314,6 +317,74 @@ wd_status retire(wd_server* sv, Pool& pl, Request& q, int r, const SolverCtl& hc
   return WD_OK;
 }
 
+// One pool: retire finished slots, release idle memory, admit, launch.
+wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory) {
+  const int prec = s->p.inner_precision;
+  Ctx& c = pl.ctx->c;
+  if (pl.launched) {
+    // retire the slots whose system finished during the step just completed
+    WS_CK(s, cudaMemcpyAsync(pl.hctl, pl.bb.ctl, pl.capacity * sizeof(SolverCtl), cudaMemcpyDeviceToHost, c.stream));
+    WS_CK(s, cudaStreamSynchronize(c.stream));
+    for (int r = 0; r < pl.capacity; ++r) {
+      if (pl.slot_req[r] < 0 || !pl.hctl[r].done) continue;
+      wd_status st = retire(s, pl, s->reqs[pl.slot_req[r]], r, pl.hctl[r]);
+      if (st != WD_OK) return st;
+    }
+    WS_CK(s, cudaStreamSynchronize(c.stream));
+    pl.launched = false;
+  }
+  bool busy = false;
+  for (long long id : pl.slot_req) busy |= (id >= 0);
+  if (pl.capacity && !busy && pl.queue.empty()) release_workspace(pl, s->used);
+  if (!pl.queue.empty() && !pl.capacity) {
+    // slot memory: what the budget has left, shared with the other pools that wait
+    const size_t left = s->p.budget_bytes ? (s->p.budget_bytes > s->used ? s->p.budget_bytes - s->used : 0)
+                                          : (size_t)-1;
+    const size_t share = s->p.budget_bytes ? left / (size_t)std::max(1, waiting_for_memory) : left;
+    int cap = s->p.max_slots;
+    while (cap > 0 && s->p.budget_bytes && slot_bytes(c, prec) * cap + small_bytes(c, cap) > share) --cap;
+    if (cap < 1 && s->p.budget_bytes && slot_bytes(c, prec) + small_bytes(c, 1) <= left) cap = 1;
+    if (cap >= 1) {
+      --waiting_for_memory;
+      wd_status st = alloc_workspace(s, pl, cap);
+      if (st != WD_OK) return st;
+    }
+  }
+  for (int r = 0; r < pl.capacity && !pl.queue.empty(); ++r) {
+    if (pl.slot_req[r] >= 0) continue;
+    const long long id = pl.queue.front();
+    pl.queue.pop_front();
+    wd_status st = admit(s, pl, s->reqs[id], r);
+    if (st != WD_OK) return st;
+  }
+  int n = 0;
+  for (long long id : pl.slot_req) n += (id >= 0);
+  if (!n) return WD_OK;
+  // up to iters_per_step lockstep iterations, then an event marks the end
+  batch_reset_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, s->p.iters_per_step, s->p.use_graph ? 1 : 0, pl.hu, pl.hl);
+  WS_CK(s, cudaGetLastError());
+  if (s->p.use_graph) {
+    WS_CK(s, cudaGraphLaunch(pl.exec, c.stream));
+  } else {
+    const PrecOps* o = prec_ops(prec);
+    BatchCtl hb;
+    for (int it = 0; it < s->p.iters_per_step; ++it) {
+      o->batch_iteration(c, pl.bl, pl.bb, c.stream);
+      WS_CK(s, cudaMemcpyAsync(&hb, pl.bb.bc, sizeof(hb), cudaMemcpyDeviceToHost, c.stream));
+      WS_CK(s, cudaStreamSynchronize(c.stream));
+      if (hb.any_update) o->batch_update(c, pl.bl, pl.bb, c.stream);
+      batch_loop_control_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, pl.bb.ctl, pl.capacity);
+      WS_CK(s, cudaMemcpyAsync(&hb, pl.bb.bc, sizeof(hb), cudaMemcpyDeviceToHost, c.stream));
+      WS_CK(s, cudaStreamSynchronize(c.stream));
+      if (hb.all_done) break;
+    }
+  }
+  if (!pl.done_ev) WS_CK(s, cudaEventCreateWithFlags(&pl.done_ev, cudaEventDisableTiming));
+  WS_CK(s, cudaEventRecord(pl.done_ev, c.stream));
+  pl.launched = true;
+  return WD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -337,6 +408,7 @@ wd_status wd_server_destroy(wd_server* s) {
   for (Pool& pl : s->pools) {
     if (pl.ctx) cudaStreamSynchronize(pl.ctx->c.stream);
     release_workspace(pl, s->used);
+    if (pl.done_ev) cudaEventDestroy(pl.done_ev);
     if (pl.ctx) {
       cudaStream_t st = pl.ctx->c.stream;
       wd_destroy(pl.ctx);
@@ -421,91 +493,40 @@ wd_status wd_server_submit(wd_server* s, int gauge_id, const double* b, double* 
 
 wd_status wd_server_step(wd_server* s, int* active_out, int* queued_out) {
   if (!s) return WD_ERR_INVALID_ARG;
-  const int prec = s->p.inner_precision;
-  // 1. retire slots whose system finished during the last step
-  for (Pool& pl : s->pools) {
-    if (!pl.capacity || !pl.launched) continue;
-    Ctx& c = pl.ctx->c;
-    WS_CK(s, cudaMemcpyAsync(pl.hctl, pl.bb.ctl, pl.capacity * sizeof(SolverCtl), cudaMemcpyDeviceToHost, c.stream));
-    WS_CK(s, cudaStreamSynchronize(c.stream));
-    for (int r = 0; r < pl.capacity; ++r) {
-      if (pl.slot_req[r] < 0) continue;
-      if (!pl.hctl[r].done) continue;
-      wd_status st = retire(s, pl, s->reqs[pl.slot_req[r]], r, pl.hctl[r]);
+  // Pools progress independently: a pool whose step is still running on its
+  // stream is left alone, so requests on small lattices are not held behind
+  // long steps on large ones.  If no pool can make progress, wait for the
+  // first running pool to finish its step, then progress again.
+  for (int pass = 0; pass < 2; ++pass) {
+    int waiting = 0;
+    for (Pool& pl : s->pools) waiting += (!pl.queue.empty() && !pl.capacity);
+    bool progressed = false;
+    for (Pool& pl : s->pools) {
+      if (pl.launched) {
+        const cudaError_t q = cudaEventQuery(pl.done_ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return serr(s, WD_ERR_CUDA, std::string("pool step: ") + cudaGetErrorString(q));
+      } else if (pl.queue.empty()) {
+        bool busy = false;
+        for (long long id : pl.slot_req) busy |= (id >= 0);
+        if (!busy && !pl.capacity) continue;
+      }
+      wd_status st = pool_progress(s, pl, waiting);
       if (st != WD_OK) return st;
+      progressed = true;
     }
-    WS_CK(s, cudaStreamSynchronize(c.stream));
-    pl.launched = false;
+    if (progressed || pass == 1) break;
+    for (Pool& pl : s->pools)
+      if (pl.launched) {
+        WS_CK(s, cudaEventSynchronize(pl.done_ev));
+        break;
+      }
   }
-  // 2. release the slot memory of idle pools
-  for (Pool& pl : s->pools) {
-    if (!pl.capacity || !pl.queue.empty()) continue;
-    bool busy = false;
-    for (long long id : pl.slot_req) busy |= (id >= 0);
-    if (!busy) release_workspace(pl, s->used);
-  }
-  // 3. admit queued requests into free slots while memory allows; pools that
-  // need slot memory share what the budget has left equally
-  int waiting = 0;
-  for (Pool& pl : s->pools) waiting += (!pl.queue.empty() && !pl.capacity);
-  for (Pool& pl : s->pools) {
-    if (pl.queue.empty()) continue;
-    if (!pl.capacity) {
-      const size_t left = s->p.budget_bytes ? (s->p.budget_bytes > s->used ? s->p.budget_bytes - s->used : 0)
-                                            : (size_t)-1;
-      const size_t share = s->p.budget_bytes ? left / (size_t)std::max(1, waiting) : left;
-      int cap = s->p.max_slots;
-      while (cap > 0 && s->p.budget_bytes &&
-             slot_bytes(pl.ctx->c, prec) * cap + small_bytes(pl.ctx->c, cap) > share)
-        --cap;
-      if (cap < 1 && share < left && s->p.budget_bytes &&
-          slot_bytes(pl.ctx->c, prec) + small_bytes(pl.ctx->c, 1) <= left)
-        cap = 1;
-      if (cap < 1) continue;  // waits until another pool frees memory
-      --waiting;
-      wd_status st = alloc_workspace(s, pl, cap);
-      if (st != WD_OK) return st;
-    }
-    for (int r = 0; r < pl.capacity && !pl.queue.empty(); ++r) {
-      if (pl.slot_req[r] >= 0) continue;
-      const long long id = pl.queue.front();
-      pl.queue.pop_front();
-      wd_status st = admit(s, pl, s->reqs[id], r);
-      if (st != WD_OK) return st;
-    }
-  }
-  // 4. run up to iters_per_step lockstep iterations on every busy pool; the
-  // pools' streams run concurrently
   int active = 0, queued = 0;
   for (Pool& pl : s->pools) {
     queued += (int)pl.queue.size();
-    int n = 0;
-    for (long long id : pl.slot_req) n += (id >= 0);
-    active += n;
-    if (!n) continue;
-    Ctx& c = pl.ctx->c;
-    batch_reset_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, s->p.iters_per_step, s->p.use_graph ? 1 : 0, pl.hu, pl.hl);
-    WS_CK(s, cudaGetLastError());
-    if (s->p.use_graph) {
-      WS_CK(s, cudaGraphLaunch(pl.exec, c.stream));
-    } else {
-      const PrecOps* o = prec_ops(prec);
-      BatchCtl hb;
-      for (int it = 0; it < s->p.iters_per_step; ++it) {
-        o->batch_iteration(c, pl.bl, pl.bb, c.stream);
-        WS_CK(s, cudaMemcpyAsync(&hb, pl.bb.bc, sizeof(hb), cudaMemcpyDeviceToHost, c.stream));
-        WS_CK(s, cudaStreamSynchronize(c.stream));
-        if (hb.any_update) o->batch_update(c, pl.bl, pl.bb, c.stream);
-        batch_loop_control_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, pl.bb.ctl, pl.capacity);
-        WS_CK(s, cudaMemcpyAsync(&hb, pl.bb.bc, sizeof(hb), cudaMemcpyDeviceToHost, c.stream));
-        WS_CK(s, cudaStreamSynchronize(c.stream));
-        if (hb.all_done) break;
-      }
-    }
-    pl.launched = true;
+    for (long long id : pl.slot_req) active += (id >= 0);
   }
-  for (Pool& pl : s->pools)
-    if (pl.launched) WS_CK(s, cudaStreamSynchronize(pl.ctx->c.stream));
   if (active_out) *active_out = active;
   if (queued_out) *queued_out = queued;
   return WD_OK;

@@ -202,7 +202,12 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
 }
 
 BatchLaunch launch_shape(const Ctx& c, int n) {
-  return BatchLaunch{n, c.batch_tr ? c.batch_tr : 4, c.batch_tr ? c.batch_grid : c.num_sms * 4, blas_gx(c, n)};
+  const int ntiles = (c.g.Vh + 31) / 32;
+  BatchLaunch bl{n, c.batch_tr ? c.batch_tr : 4, c.batch_tr ? c.batch_grid : c.num_sms * 4, blas_gx(c, n)};
+  if (bl.grid > ntiles) bl.grid = ntiles;
+  bl.tr64 = 8;
+  bl.grid64 = c.num_sms * 4 < ntiles ? c.num_sms * 4 : ntiles;
+  return bl;
 }
 
 wd_status build_batch_graph(wd_ctx* ctx, int prec, BatchBufs& b, const BatchLaunch& bl) {
@@ -223,6 +228,7 @@ wd_status solve_batch_device(wd_ctx* ctx, int n, void* x, const void* bsrc, cons
   if (p.inner_precision < WD_F64 || p.inner_precision > WD_B16N)
     return berr(ctx, WD_ERR_INVALID_ARG, "bad inner_precision");
   if (p.solver != WD_BICGSTAB) return berr(ctx, WD_ERR_INVALID_ARG, "batched solves use BiCGstab");
+  if (p.restart) return berr(ctx, WD_ERR_INVALID_ARG, "batched solves use reliable updates (restart = 0)");
   if (!(p.tol > 0.0) || p.max_iter <= 0) return berr(ctx, WD_ERR_INVALID_ARG, "bad tol or max_iter");
   if (p.inner_precision == WD_F64) p.delta = 0.0;
   else if (!(p.delta > 0.0 && p.delta < 1.0)) return berr(ctx, WD_ERR_INVALID_ARG, "delta must be in (0,1)");
@@ -256,7 +262,7 @@ wd_status solve_batch_device(wd_ctx* ctx, int n, void* x, const void* bsrc, cons
     if ((st = tune_batch(ctx, n, p.inner_precision, b)) != WD_OK) return st;
   }
   const BatchLaunch bl = launch_shape(c, n);
-  const BatchArgs all{n, nullptr, 0, b.partials};
+  const BatchArgs all{n, nullptr, 0, b.partials, nullptr};
   // |b_e|^2, |b_o|^2 per system
   launch_sites_batch(g, bl, OpNorm2<SpinorF64>{be, c.red, FinStore{b.scal, 1}}, all, s);
   launch_finalize<1>(bl, all, bl.blas_gx, FinStore{b.scal, 1}, b.bc, 0, 0, s);
@@ -304,10 +310,10 @@ wd_status solve_batch_device(wd_ctx* ctx, int n, void* x, const void* bsrc, cons
   const Coef nk{0.0, b.kappas + n, 1};
   EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> re{xe, false, be, xe, nk, c.red, FinStore{b.scal + 2 * n, 1}};
   launch_dslash_mrhs<double>(g, bl, xo, T64::gauge(c), 0, 0, re, all, s);
-  launch_finalize<1>(bl, all, bl.grid, FinStore{b.scal + 2 * n, 1}, b.bc, 0, 0, s);
+  launch_finalize<1>(bl, all, mrhs_grid<double>(bl), FinStore{b.scal + 2 * n, 1}, b.bc, 0, 0, s);
   EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> ro{xo, false, bo, xo, nk, c.red, FinStore{b.scal + 3 * n, 1}};
   launch_dslash_mrhs<double>(g, bl, xe, T64::gauge(c), 1, 0, ro, all, s);
-  launch_finalize<1>(bl, all, bl.grid, FinStore{b.scal + 3 * n, 1}, b.bc, 0, 0, s);
+  launch_finalize<1>(bl, all, mrhs_grid<double>(bl), FinStore{b.scal + 3 * n, 1}, b.bc, 0, 0, s);
   WB_CK_LAUNCH(ctx);
   SolverCtl* hc = (SolverCtl*)c.batch_host;
   double* hs = (double*)((char*)c.batch_host + (size_t)n * sizeof(SolverCtl));

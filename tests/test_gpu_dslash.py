@@ -9,7 +9,7 @@ import pytest
 
 import lattice_inputs as li
 import oracle
-from tests.wd_testutil import TOL, parity_mask, parity_sites, rel_err, split16
+from tests.wd_testutil import TOL, parity_mask, parity_sites, rel_err, split16, to_host_basis, to_internal_basis
 
 pytestmark = pytest.mark.gpu
 
@@ -105,7 +105,8 @@ def test_codec_bitwise(wdp, prec, fmt):
     f = wd.upload(psi, prec, parity=0)
     codes, norms = split16(f.cpu().numpy(), dims)
     sites = parity_sites(dims, 0)
-    ocodes, ovals, onorms = oracle.encode_spinor(psi[sites], fmt)
+    # the library stores S psi (App. B basis change at the boundary)
+    ocodes, ovals, onorms = oracle.encode_spinor(to_internal_basis(psi[sites]), fmt)
     np.testing.assert_array_equal(norms, onorms)
     if fmt == oracle.FMT_Q16:
         np.testing.assert_array_equal(codes.view(np.int16), ocodes)
@@ -115,9 +116,9 @@ def test_codec_bitwise(wdp, prec, fmt):
         as_f32 = (codes.astype(np.uint32) << 16).view(np.float32)
         np.testing.assert_array_equal(as_f32, ovals)
     # export decodes exactly as the oracle's decode
-    got = wd.download(f, prec, parity=0)[sites].reshape(-1, 12).view(np.float64)
-    want = oracle.decode_spinor(ocodes, ovals, onorms, fmt)
-    np.testing.assert_array_equal(got, want)
+    got = wd.download(f, prec, parity=0)[sites]
+    dec = oracle.decode_spinor(ocodes, ovals, onorms, fmt).view(np.complex128).reshape(-1, 4, 3)
+    np.testing.assert_array_equal(got, to_host_basis(dec))
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -139,7 +140,8 @@ def test_f32_export_roundtrip(wdp):
     f = wd.upload(psi, 1, parity=0)
     got = wd.download(f, 1, parity=0)
     sites = parity_sites(dims, 0)
-    np.testing.assert_array_equal(got[sites], psi[sites].astype(np.complex64).astype(np.complex128))
+    internal = to_internal_basis(psi[sites]).astype(np.complex64).astype(np.complex128)
+    np.testing.assert_array_equal(got[sites], to_host_basis(internal))
 
 
 def test_free_field_plane_wave(wdp):

@@ -159,3 +159,19 @@ def test_full_size_24x64_mixed_vs_fp64(solver, kappa):
     # Sec. 5.4: reliable updates cost a modest number of extra iterations
     assert iters[2] <= 1.5 * iters[0] + 20
     wd.close()
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("prec,eps_in", [(2, 0.1), (2, 0.01), (1, 1e-3), (1, 1e-5)])
+def test_defect_correction_alg1(small, solver, prec, eps_in):
+    """Alg. 1: inner solves to eps_in with a restart at each FP64 correction;
+    it reaches the FP64 tolerance like the reliable-update scheme."""
+    m, wd, dims, kappa, U, b, x_ref, oracle_iters = small
+    x = np.zeros_like(b)
+    r = wd.solve(x, b, kappa, tol=1e-12, delta=eps_in, solver=solver, inner_precision=prec, restart=True)
+    rel = oracle.true_residual(x, b, U, dims, kappa)
+    assert r.status == 0 and rel <= 1e-12, (r, rel)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-9
+    assert r.reliable_updates >= 1
+    with pytest.raises(m.WDError):
+        wd.solve(x, b, kappa, inner_precision=0, restart=True)

@@ -38,3 +38,32 @@ def split16(raw: np.ndarray, dims):
     off = align256(48 * st)
     norms = raw[off: off + 4 * vh].view(np.float32)
     return codes, norms
+
+
+# App. B basis change used inside the library: psi_int = S psi_DR, S real
+# orthogonal (pinned against the printed projector sets in test_basis_change.py).
+R2 = 0.70710678118654752440
+
+
+def to_internal_basis(psi):
+    """(V, 4, 3) DeGrand-Rossi -> internal basis, in the library's operation order."""
+    p = np.asarray(psi)
+    out = np.empty_like(p)
+    out[:, 0] = R2 * (p[:, 1] + p[:, 3])
+    out[:, 1] = -R2 * (p[:, 0] + p[:, 2])
+    out[:, 2] = R2 * (p[:, 1] - p[:, 3])
+    out[:, 3] = R2 * (p[:, 2] - p[:, 0])
+    return out
+
+
+def to_host_basis(v):
+    u = np.asarray(v)
+    out = np.empty_like(u)
+    out[:, 0] = -R2 * (u[:, 1] + u[:, 3])
+    out[:, 1] = R2 * (u[:, 0] + u[:, 2])
+    out[:, 2] = R2 * (u[:, 3] - u[:, 1])
+    out[:, 3] = R2 * (u[:, 0] - u[:, 2])
+    return out
+
+
+S_MATRIX = R2 * np.array([[0, 1, 0, 1], [-1, 0, -1, 0], [0, 1, 0, -1], [-1, 0, 1, 0]], dtype=np.float64)
