@@ -44,6 +44,11 @@ METRIC = "dslash GB/s vs HBM peak; mixed vs FP64 solve time to |r|/|b|<=1e-12"
 # one input spinor, one output spinor (each link and input read once)
 BYTES_PER_SITE = {0: 8 * 96 + 192 + 192, 1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 52, 3: 8 * 24 + 52 + 52,
                   4: 8 * 24 + 52 + 52}
+
+
+def bytes_per_site(prec, recon):
+    """Compulsory bytes of one output site; FP64 links hold ``recon`` reals."""
+    return 8 * 8 * recon + 384 if prec == 0 else BYTES_PER_SITE[prec]
 FLOPS_PER_SITE = 1320  # the paper's effective count (Sec. 4.3)
 # FP64 FMA peak of one GB300, measured with an FMA-throughput loop (1.252 TFLOP/s);
 # the unit count agrees: 2 FP64 FMA lanes per SM per clock x 2 flops x 152 SMs
@@ -200,13 +205,17 @@ def run_reference(args):
     return 0
 
 
-def time_dslash(wd, torch, prec, n, flush=None):
+def time_dslash(wd, torch, prec, n, flush=None, psi=None):
     """Average device time of one dslash launch (CUDA events on the
-    library's stream), optionally flushing L2 between launches."""
+    library's stream), optionally flushing L2 between launches.  The input
+    is the host spinor ``psi`` (odd sites) when given, else zeros."""
     import paper_0911_3191_gb300 as wdp
-    fin = wd.new_field(prec)
+    if psi is not None:
+        fin = wd.upload(psi, prec, parity=wdp.ODD)
+    else:
+        fin = wd.new_field(prec)
+        fin.zero_()
     fout = wd.new_field(prec)
-    fin.zero_()
     s = wd.stream
     for _ in range(3):
         wd.dslash(fout, fin, wdp.EVEN, False, prec)
@@ -324,15 +333,15 @@ def run_ours(args):
     # CUDA events on the library's stream, same lattice and launch
     # configuration as inside the solve, L2 flushed between launches.
     vh = V // 2
-    t64 = time_dslash(wd, torch, wdp.F64, 20, flush=flush)
+    t64 = time_dslash(wd, torch, wdp.F64, 20, flush=flush, psi=b)
     f64_tflops = FLOPS_PER_SITE * vh / t64 / 1e12
     traffic = NCU_TRAFFIC_BYTES.get(("f64", args.recon, "x".join(map(str, dims))))
     roofline = {"bound": "alu", "achieved": round(f64_tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(f64_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                "algorithmic_bytes": (8 * (16 * args.recon // 2) + 384) * vh, "peak_source": "measured FP64 FMA",
+                "algorithmic_bytes": bytes_per_site(0, args.recon) * vh, "peak_source": "measured FP64 FMA",
                 "kernel": f"dslash f64 {args.recon}-real (reliable update), {dims[0]}^3x{dims[3]}, {vh} sites/launch, "
                           f"1320 flops/site", "us_per_launch": round(t64 * 1e6, 2)}
-    t_ds = time_dslash(wd, torch, inner, 50, flush=flush)
+    t_ds = time_dslash(wd, torch, inner, 50, flush=flush, psi=b)
     hbm, src = peaks()
     achieved = BYTES_PER_SITE[inner] * vh / t_ds / 1e9
     dslash_roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -384,17 +393,69 @@ def dslash_sweep(torch, args):
     wd = wdp.WilsonDirac(dims)
     wd.load_gauge(U, recon=args.recon)
     del U
+    psi = li.gaussian_spinor(dims, 2102)
     hbm, src = peaks()
-    out = {"lattice": "x".join(map(str, dims)), "gauge_gen_s": round(gen_s, 1)}
+    out = {"lattice": "x".join(map(str, dims)), "gauge_gen_s": round(gen_s, 1), "fp64_link_reals": args.recon,
+           "input": "Gaussian spinor"}
     for prec in (0, 1, 2, 3, 4):
-        t = time_dslash(wd, torch, prec, 20)
-        gbs = BYTES_PER_SITE[prec] * (V // 2) / t / 1e9
+        t = time_dslash(wd, torch, prec, 20, psi=psi)
+        gbs = bytes_per_site(prec, args.recon) * (V // 2) / t / 1e9
         out[PREC_NAME[prec]] = {"us": round(t * 1e6, 1), "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
                                 "eff_gflops": round(FLOPS_PER_SITE * (V // 2) / t / 1e9, 1)}
     out["peak_gbs"] = hbm
     out["peak_source"] = src
     wd.close()
     return out
+
+
+def run_table(args):
+    """The solver comparison on the 24^3x64 lattice (links exp(0.3 i H)):
+    kappa in {0.12, 0.124} x 3 Gaussian sources x {BiCGstab, CGNR} x
+    {pure FP64; reliable updates (Alg. 2, delta 0.1) with F32, Q16, H16N, B16N
+    inner; defect correction (Alg. 1) with Q16 inner at eps_in 1e-1, 1e-2 and
+    F32 inner at eps_in 1e-3 .. 1e-6}, all to |r|/|b| <= 1e-12.  Each entry:
+    device time of one solve (inputs resident, L2 flushed), iterations
+    (reliable updates / corrections included), FP64 updates, true residual."""
+    import torch
+
+    import lattice_inputs as li
+    import paper_0911_3191_gb300 as wdp
+    dims = WORKLOAD["dims"]
+    U = li.gauge(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
+    wd = wdp.WilsonDirac(dims)
+    wd.load_gauge(U, recon=args.recon)
+    del U
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fx = wd.new_field(wdp.F64, 2)
+    variants = [("fp64", wdp.F64, 0.1, False)]
+    variants += [(f"ru-{n}", p, 0.1, False) for n, p in (("f32", wdp.F32), ("q16", wdp.Q16), ("h16n", wdp.H16N),
+                                                         ("b16n", wdp.B16N))]
+    variants += [(f"dc-q16-{e:g}", wdp.Q16, e, True) for e in (1e-1, 1e-2)]
+    variants += [(f"dc-f32-{e:g}", wdp.F32, e, True) for e in (1e-3, 1e-4, 1e-5, 1e-6)]
+    rows = []
+    for kappa in (0.12, 0.124):
+        for seed in (2001, 2011, 2021):
+            fb = wd.upload(li.gaussian_spinor(dims, seed), wdp.F64)
+            for solver_name, solver in (("bicgstab", wdp.BICGSTAB), ("cgnr", wdp.CGNR)):
+                for name, prec, delta, restart in variants:
+                    def go():
+                        return wd.solve_device(fx, fb, kappa, tol=1e-12, delta=delta, max_iter=4000,
+                                               solver=solver, inner_precision=prec, restart=restart, check=False)
+                    go()  # graph capture and tuning outside the timing
+                    flush.add_(1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(wd.stream)
+                    r = go()
+                    e1.record(wd.stream)
+                    e1.synchronize()
+                    rows.append({"kappa": kappa, "source_seed": seed, "solver": solver_name, "variant": name,
+                                 "ms": round(e0.elapsed_time(e1), 3), "iters": r.iters,
+                                 "updates": r.reliable_updates, "true_rel_residual": r.true_rel_residual,
+                                 "status": r.status})
+            del fb
+    wd.close()
+    print(json.dumps({"table": "24x24x24x64 eps=0.3 solver comparison, tol 1e-12", "rows": rows}))
+    return 0
 
 
 def run_dslash_only(args):
@@ -406,15 +467,22 @@ def run_dslash_only(args):
     prec = wdp.PREC_BY_NAME[args.dslash_only]
     wd = wdp.WilsonDirac(dims)
     wd.load_gauge(li.gauge(dims, 0.3, 1002), recon=args.recon)
-    fin = wd.new_field(prec)
-    fin.zero_()
+    fin = wd.upload(li.gaussian_spinor(dims, 2102), prec, parity=wdp.ODD)
     fout = wd.new_field(prec)
     for _ in range(args.warmup + args.steps):
         wd.dslash(fout, fin, wdp.EVEN, False, prec)
     torch.cuda.synchronize()
-    t = time_dslash(wd, torch, prec, max(1, args.steps))
+    ts = []
+    for _ in range(max(1, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(wd.stream)
+        wd.dslash(fout, fin, wdp.EVEN, False, prec)
+        e1.record(wd.stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1000.0)
+    t = statistics.mean(ts)
     vh = li.volume(dims) // 2
-    gbs = BYTES_PER_SITE[prec] * vh / t / 1e9
+    gbs = bytes_per_site(prec, args.recon) * vh / t / 1e9
     print(json.dumps({"dslash": args.dslash_only, "lattice": "x".join(map(str, dims)), "us": round(t * 1e6, 2),
                       "GB/s": round(gbs, 1), "frac": round(gbs / peaks()[0], 4)}))
     return 0
@@ -640,6 +708,8 @@ def main():
                     help="time only the dslash of one precision on --sweep-dims (profiling case)")
     ap.add_argument("--batch", action="store_true", help="batched 48-system multi-RHS solve (32^3x64)")
     ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream")
+    ap.add_argument("--table", action="store_true",
+                    help="solver comparison table on 24^3x64 (reliable update vs defect correction vs FP64)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-iters", type=int, default=8)
@@ -648,6 +718,8 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.table:
+        return run_table(args)
     if args.dslash_only:
         return run_dslash_only(args)
     if args.impl == "reference":
