@@ -64,6 +64,8 @@ def _load():
                 "wo_encode_spinor": (None, [dp, c_i64, c_int, i16p, fp, fp]),
                 "wo_decode_spinor": (None, [i16p, fp, fp, c_i64, c_int, dp]),
                 "wo_encode_link_values": (None, [dp, c_i64, c_int, i16p, dp]),
+                "wo_su3_to8": (c_int, [dp, dp]),
+                "wo_su3_from8": (None, [dp, dp]),
                 "wo_round_fp16": (ctypes.c_float, [ctypes.c_float]),
                 "wo_round_bf16": (ctypes.c_float, [ctypes.c_float]),
             }
@@ -166,7 +168,7 @@ def true_residual(x, b, U, dims, kappa, tbc_anti=False) -> float:
 
 
 def encode_spinor(v, fmt: int):
-    """Per-site 16-bit codec (Sec. 4.5).  ``v``: (n, 24) or (n, 4, 3) complex.
+    """Per-site 16-bit codec (Sec. 4.6).  ``v``: (n, 24) or (n, 4, 3) complex.
 
     Returns (codes int16 (n, 24) for Q16 else None, rounded values float32
     (n, 24) for H16N/B16N else None, norms float32 (n,))."""
@@ -223,3 +225,32 @@ def round_fp16(w: float) -> float:
 
 def round_bf16(w: float) -> float:
     return float(_load().wo_round_bf16(float(w)))
+
+
+def su3_to8(U) -> tuple:
+    """App. A.2: links (..., 3, 3) -> (p (..., 8), singular (...,) bool)."""
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    flat = U.reshape(-1, 9)
+    p = np.empty((len(flat), 8), dtype=np.float64)
+    sing = np.empty(len(flat), dtype=bool)
+    lib = _load()
+    for i in range(len(flat)):
+        row = np.ascontiguousarray(flat[i])
+        out = np.empty(8)
+        sing[i] = bool(lib.wo_su3_to8(_p(row.view(np.float64)), _p(out)))
+        p[i] = out
+    return p.reshape(U.shape[:-2] + (8,)), sing.reshape(U.shape[:-2])
+
+
+def su3_from8(p) -> np.ndarray:
+    """App. A.2: (..., 8) parameters -> links (..., 3, 3)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    flat = p.reshape(-1, 8)
+    out = np.empty((len(flat), 9), dtype=np.complex128)
+    lib = _load()
+    for i in range(len(flat)):
+        row = np.ascontiguousarray(flat[i])
+        o = np.empty(9, dtype=np.complex128)
+        lib.wo_su3_from8(_p(row), _p(o.view(np.float64)))
+        out[i] = o
+    return out.reshape(p.shape[:-1] + (3, 3))

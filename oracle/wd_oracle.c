@@ -21,7 +21,8 @@
  *   Sec. 3 Schur complement   : M_hat = 1 - kappa^2 D_eo D_oe (wo_apply_Mhat)
  *   App. B DeGrand-Rossi set  : the projectors P^{+mu} (wo_projector)
  *   Sec. 5.1                  : CG on the normal equations, BiCGstab
- *   Sec. 4.5 (half precision) : per-site-normalised 16-bit storage codecs
+ *   Sec. 4.6 (half precision) : per-site-normalised 16-bit storage codecs
+ *   App. A.2                  : the 8-number SU(3) parametrisation (wo_su3_to8/from8)
  *
  * Boundary conditions (paper silent): periodic in all directions; optionally
  * antiperiodic in t, i.e. a factor -1 on every hop that crosses t = T-1 <-> 0.
@@ -434,7 +435,7 @@ double wo_bicgstab_schur_iters(const double *b_in, const double *U, const int di
 }
 
 /* ------------------------------------------------------------------ codecs
- * Sec. 4.5: a colour-spinor is stored as 24 16-bit numbers plus one FP32
+ * Sec. 4.6: a colour-spinor is stored as 24 16-bit numbers plus one FP32
  * number standing for its largest element.  The encode is defined in FP32
  * arithmetic (the arithmetic of the kernels that produce these fields):
  *   f_k  = (float) v_k                       (round to nearest even)
@@ -530,5 +531,47 @@ void wo_encode_link_values(const double *u, int64_t n, int fmt, int16_t *codes, 
       codes[i] = 0;
       decoded[i] = (double)r;
     }
+  }
+}
+
+/* ---- App. A.2: 8-number parametrisation of an SU(3) link -----------------
+ * Rows a, b, c of U.  Stored: p = {arg a1, arg c1, Re a2, Im a2, Re a3,
+ * Im a3, Re b1, Im b1}.  Reconstruction, in the appendix's order:
+ *   1. |a1| from the unit norm of row a, a1 = |a1| e^{i arg a1};
+ *   2. |c1| from the unit norm of column 1, c1 = |c1| e^{i arg c1};
+ *   3. with N = sqrt(|a2|^2 + |a3|^2), the unit vectors b' = (0, -a3^*, a2^*)/N
+ *      and c' = (a x b')^* = (N, -a1^* a2/N, -a1^* a3/N) span the plane
+ *      orthogonal to a (the appendix's matrix prints b' with a different
+ *      sign and conjugation on its last entry; this b' is the one orthogonal
+ *      to a: a . conj(b') = (-a2 a3 + a3 a2)/N = 0);
+ *   4. rows b and c are the SU(2) rotation of (b', c'): with p2 = b1/N and
+ *      p1 = conj(c1)/N, b = p1 b' + p2 c', c = -p2^* b' + p1^* c'.
+ * Singular at N = 0 (|a1| = 1): to8 returns 1 there. */
+int wo_su3_to8(const double *u, double *p) {
+  const cd *U = (const cd *)u;
+  p[0] = carg(U[0]);
+  p[1] = carg(U[6]);
+  p[2] = creal(U[1]); p[3] = cimag(U[1]);
+  p[4] = creal(U[2]); p[5] = cimag(U[2]);
+  p[6] = creal(U[3]); p[7] = cimag(U[3]);
+  const double n2 = creal(U[1] * conj(U[1])) + creal(U[2] * conj(U[2]));
+  return n2 > 0.0 ? 0 : 1;
+}
+
+void wo_su3_from8(const double *p, double *u) {
+  cd *U = (cd *)u;
+  const cd a2 = p[2] + I * p[3], a3 = p[4] + I * p[5], b1 = p[6] + I * p[7];
+  const double n2 = creal(a2 * conj(a2)) + creal(a3 * conj(a3));
+  const cd a1 = sqrt(fmax(0.0, 1.0 - n2)) * cexp(I * p[0]);
+  const double b12 = creal(b1 * conj(b1));
+  const cd c1 = sqrt(fmax(0.0, 1.0 - creal(a1 * conj(a1)) - b12)) * cexp(I * p[1]);
+  const double N = sqrt(n2);
+  const cd bp[3] = {0.0, -conj(a3) / N, conj(a2) / N};
+  const cd cp[3] = {N, -conj(a1) * a2 / N, -conj(a1) * a3 / N};
+  const cd p2 = b1 / N, p1 = conj(c1) / N;
+  U[0] = a1; U[1] = a2; U[2] = a3;
+  for (int j = 0; j < 3; ++j) {
+    U[3 + j] = p1 * bp[j] + p2 * cp[j];
+    U[6 + j] = -conj(p2) * bp[j] + conj(p1) * cp[j];
   }
 }

@@ -78,3 +78,43 @@ def test_mutation_is_caught(name, lattice, tmp_path, monkeypatch):
             caught += 1
     assert caught > 0, f"no pin caught the planted mistake: {name}"
     assert np.isfinite(caught)
+
+
+CODEC_MUTATIONS = {
+    # the appendix's printed matrix: b' = (0, -a3^*/N, -a2^*/N), not orthogonal to a
+    "8-number b' as printed in the matrix": ("{0.0, -conj(a3) / N, conj(a2) / N}",
+                                            "{0.0, -conj(a3) / N, -conj(a2) / N}"),
+    "8-number p1 not conjugated": ("p1 = conj(c1) / N", "p1 = c1 / N"),
+    "8-number column norm of c1 without |b1|": ("- creal(a1 * conj(a1)) - b12", "- creal(a1 * conj(a1))"),
+}
+
+
+@pytest.mark.parametrize("name", list(CODEC_MUTATIONS))
+def test_codec_mutation_is_caught(name, tmp_path, monkeypatch):
+    old, new = CODEC_MUTATIONS[name]
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old}"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    so = str(tmp_path / "mut.so")
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                           "-fcx-limited-range", "-o", so, str(path), "-lm"])
+    good = oracle._load()
+    mutated = ctypes.CDLL(so)
+    for fname in ("wo_su3_to8", "wo_su3_from8"):
+        f, g = getattr(mutated, fname), getattr(good, fname)
+        f.argtypes, f.restype = g.argtypes, g.restype
+
+    class Shim:
+        def __getattr__(self, item):
+            return getattr(mutated, item) if item in ("wo_su3_to8", "wo_su3_from8") else getattr(good, item)
+
+    monkeypatch.setattr(oracle, "_lib", Shim())
+    caught = 0
+    for chk in (lambda: pins.test_su3_8number_roundtrip(3.0),
+                pins.test_su3_8number_rebuilds_su3_from_any_valid_parameters):
+        try:
+            chk()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, f"no pin caught the planted mistake: {name}"

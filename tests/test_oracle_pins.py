@@ -344,3 +344,42 @@ def test_generated_links_are_su3_with_third_row_from_first_two():
     # eps controls the distance from the unit matrix
     U2 = li.gauge((4, 4, 4, 8), 0.05, 1002).reshape(-1, 3, 3)
     assert np.abs(U2 - np.eye(3)).mean() < np.abs(U - np.eye(3)).mean()
+
+
+# ---- App. A.2: the 8-number parametrisation
+@pytest.mark.parametrize("eps", [0.3, 1.0, 3.0])
+def test_su3_8number_roundtrip(eps):
+    """Encoding a link into (arg a1, arg c1, a2, a3, b1) and rebuilding it
+    gives the link back (away from the singularity |a1| = 1)."""
+    U = li.su3_field(500, eps, 77).reshape(-1, 3, 3)
+    p, sing = oracle.su3_to8(U)
+    assert not sing.any()
+    N = np.sqrt(np.abs(U[:, 0, 1]) ** 2 + np.abs(U[:, 0, 2]) ** 2)
+    err = np.abs(oracle.su3_from8(p) - U).max(axis=(1, 2))
+    assert np.all(err <= 1e-14 / N)
+
+
+def test_su3_8number_rebuilds_su3_from_any_valid_parameters():
+    """Any parameters in the valid region give a special unitary matrix whose
+    stored entries are the given ones (|a1|, |c1| from unit row / column)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        a2, a3 = (rng.normal(size=2) @ [1, 1j]) * 0.5, (rng.normal(size=2) @ [1, 1j]) * 0.5
+        s = abs(a2) ** 2 + abs(a3) ** 2
+        if s >= 0.99:
+            continue
+        b1 = (rng.normal(size=2) @ [1, 1j])
+        b1 *= rng.uniform(0, 1) * np.sqrt(s) / abs(b1)  # |b1|^2 <= 1 - |a1|^2 = s
+        p = np.array([rng.uniform(-np.pi, np.pi), rng.uniform(-np.pi, np.pi), a2.real, a2.imag, a3.real, a3.imag,
+                      b1.real, b1.imag])
+        U = oracle.su3_from8(p)
+        np.testing.assert_allclose(U @ U.conj().T, np.eye(3), atol=1e-13)
+        assert abs(np.linalg.det(U) - 1) < 1e-13
+        assert abs(U[0, 1] - a2) < 1e-15 and abs(U[0, 2] - a3) < 1e-15 and abs(U[1, 0] - b1) < 1e-15
+        assert abs(np.angle(U[0, 0]) - p[0]) % (2 * np.pi) < 1e-12 or abs(U[0, 0]) < 1e-12
+
+
+def test_su3_8number_singularity_flagged():
+    assert oracle.su3_to8(np.eye(3, dtype=np.complex128))[1]
+    D = np.diag(np.exp(1j * np.array([0.3, -0.5, 0.2])))
+    assert oracle.su3_to8(D)[1]
