@@ -46,9 +46,25 @@ BYTES_PER_SITE = {0: 8 * 96 + 192 + 192, 1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 5
                   4: 8 * 24 + 52 + 52}
 
 
-def bytes_per_site(prec, recon):
-    """Compulsory bytes of one output site; FP64 links hold ``recon`` reals."""
-    return 8 * 8 * recon + 384 if prec == 0 else BYTES_PER_SITE[prec]
+def bytes_per_site(prec, recon, tfix=False, recon8=False):
+    """Compulsory bytes of one output site: the links read (8, or 6 in the
+    temporal gauge, asymptotically: the last time slice still reads its
+    temporal links), one input and one output spinor; FP64 links hold
+    ``recon`` reals, FP32 / 16-bit links 12 reals or 8 numbers (recon8)."""
+    if prec == 0:
+        link = 8 * recon
+    else:
+        link = {1: 48, 2: 24, 3: 24, 4: 24}[prec] * (8 if recon8 else 12) // 12
+    spinor = {0: 192, 1: 96, 2: 52, 3: 52, 4: 52}[prec]
+    return (6 if tfix else 8) * link + 2 * spinor
+
+
+def flops_per_site(tfix=False):
+    """The paper's 1320 flops per site; the temporal gauge removes the two
+    temporal SU(3) multiplies (2 x 132 flops) away from the last time slice."""
+    return FLOPS_PER_SITE - (2 * 132 if tfix else 0)
+
+
 FLOPS_PER_SITE = 1320  # the paper's effective count (Sec. 4.3)
 # FP64 FMA peak of one GB300, measured with an FMA-throughput loop (1.252 TFLOP/s);
 # the unit count agrees: 2 FP64 FMA lanes per SM per clock x 2 flops x 152 SMs
@@ -60,7 +76,8 @@ FP64_PEAK_TFLOPS = 1.252
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --set full,
 # the dslash-only command of this file at 24^3x64); None where not captured
 # since the kernel last changed.
-NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64"): 650.13e6, ("q16", 12, "24x24x24x64"): 112.31e6}
+# key: (precision, link reals, lattice, temporal gauge)
+NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", False): 650.13e6, ("q16", 12, "24x24x24x64", False): 112.31e6}
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
 
@@ -249,7 +266,7 @@ def run_ours(args):
     U = li.gauge(dims, W["eps"], W["gauge_seed"])
     b = li.gaussian_spinor(dims, W["source_seed"])
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(U, recon=args.recon)
+    wd.load_gauge(U, recon=args.recon, temporal_gauge=args.temporal_gauge, recon8=args.recon8)
     s = wd.stream
     fb = wd.upload(b, wdp.F64)
     fx = wd.new_field(wdp.F64, 2)
@@ -334,29 +351,35 @@ def run_ours(args):
     # configuration as inside the solve, L2 flushed between launches.
     vh = V // 2
     t64 = time_dslash(wd, torch, wdp.F64, 20, flush=flush, psi=b)
-    f64_tflops = FLOPS_PER_SITE * vh / t64 / 1e12
-    traffic = NCU_TRAFFIC_BYTES.get(("f64", args.recon, "x".join(map(str, dims))))
+    tf = args.temporal_gauge
+    f64_tflops = flops_per_site(tf) * vh / t64 / 1e12
+    traffic = NCU_TRAFFIC_BYTES.get(("f64", args.recon, "x".join(map(str, dims)), tf))
     roofline = {"bound": "alu", "achieved": round(f64_tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(f64_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                "algorithmic_bytes": bytes_per_site(0, args.recon) * vh, "peak_source": "measured FP64 FMA",
-                "kernel": f"dslash f64 {args.recon}-real (reliable update), {dims[0]}^3x{dims[3]}, {vh} sites/launch, "
-                          f"1320 flops/site", "us_per_launch": round(t64 * 1e6, 2)}
+                "algorithmic_bytes": bytes_per_site(0, args.recon, tf) * vh, "peak_source": "measured FP64 FMA",
+                "kernel": f"dslash f64 {args.recon}-real (reliable update){' temporal gauge' if tf else ''}, "
+                          f"{dims[0]}^3x{dims[3]}, {vh} sites/launch, {flops_per_site(tf)} flops/site",
+                "us_per_launch": round(t64 * 1e6, 2)}
     t_ds = time_dslash(wd, torch, inner, 50, flush=flush, psi=b)
     hbm, src = peaks()
-    achieved = BYTES_PER_SITE[inner] * vh / t_ds / 1e9
+    achieved = bytes_per_site(inner, 12, tf, args.recon8) * vh / t_ds / 1e9
     dslash_roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                        "frac": round(achieved / hbm, 4),
-                       "traffic": NCU_TRAFFIC_BYTES.get((args.inner, 12, "x".join(map(str, dims)))),
+                       "traffic": NCU_TRAFFIC_BYTES.get((args.inner, 8 if args.recon8 else 12, "x".join(map(str, dims)), tf)),
                        "peak_source": src,
-                       "kernel": f"dslash {args.inner} 12-real (inner iteration), {dims[0]}^3x{dims[3]}, {vh} "
-                                 f"sites/launch, {BYTES_PER_SITE[inner]} B/site algorithmic",
+                       "kernel": f"dslash {args.inner} {'8-number' if args.recon8 else '12-real'} (inner iteration), "
+                                 f"{dims[0]}^3x{dims[3]}, {vh} "
+                                 f"sites/launch, {bytes_per_site(inner, 12, tf, args.recon8)} B/site algorithmic"
+                                 f"{' (temporal gauge)' if tf else ''}",
                        "us_per_launch": round(t_ds * 1e6, 2)}
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1000 * t_total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.inner + "+f64", "data": "synthetic",
             "config": {"workload": W["workload"], "lattice": "24x24x24x64", "solver": args.solver,
-                       "fp64_link_reals": args.recon, "loop": "host" if args.host_loop else "cuda-graph",
+                       "fp64_link_reals": args.recon, "temporal_gauge": args.temporal_gauge,
+                       "low_precision_links": "8 numbers" if args.recon8 else "12 reals",
+                       "loop": "host" if args.host_loop else "cuda-graph",
                        "inner_precision": args.inner, "parallelism": f"replicas{ws}",
                        "l2": "flushed between timed solves (256 MB write); inputs (FP64 gauge 340 MB) exceed L2"},
             "solve": {"iters": r0.iters, "reliable_updates": r0.reliable_updates,
@@ -390,21 +413,25 @@ def dslash_sweep(torch, args):
     t0 = time.perf_counter()
     U = li.gauge(dims, 0.3, 1002)
     gen_s = time.perf_counter() - t0
-    wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(U, recon=args.recon)
-    del U
     psi = li.gaussian_spinor(dims, 2102)
     hbm, src = peaks()
     out = {"lattice": "x".join(map(str, dims)), "gauge_gen_s": round(gen_s, 1), "fp64_link_reals": args.recon,
-           "input": "Gaussian spinor"}
-    for prec in (0, 1, 2, 3, 4):
-        t = time_dslash(wd, torch, prec, 20, psi=psi)
-        gbs = bytes_per_site(prec, args.recon) * (V // 2) / t / 1e9
-        out[PREC_NAME[prec]] = {"us": round(t * 1e6, 1), "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
-                                "eff_gflops": round(FLOPS_PER_SITE * (V // 2) / t / 1e9, 1)}
-    out["peak_gbs"] = hbm
-    out["peak_source"] = src
-    wd.close()
+           "input": "Gaussian spinor", "peak_gbs": hbm, "peak_source": src}
+    # link storage variants: general links; temporal gauge; temporal gauge
+    # with the 8-number FP32 / 16-bit links (the paper's "8 GF")
+    for tf, r8 in ((False, False), (True, False), (True, True)):
+        wd = wdp.WilsonDirac(dims)
+        wd.load_gauge(U, recon=args.recon, temporal_gauge=tf, recon8=r8)
+        for prec in (0, 1, 2, 3, 4):
+            if r8 and prec == 0:
+                continue
+            t = time_dslash(wd, torch, prec, 20, psi=psi)
+            nbytes = bytes_per_site(prec, args.recon, tf, r8)
+            gbs = nbytes * (V // 2) / t / 1e9
+            out[PREC_NAME[prec] + ("_temporal_gauge" if tf else "") + ("_recon8" if r8 else "")] = {
+                "us": round(t * 1e6, 1), "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4), "bytes_per_site": nbytes,
+                "eff_gflops": round(flops_per_site(tf) * (V // 2) / t / 1e9, 1)}
+        wd.close()
     return out
 
 
@@ -423,7 +450,7 @@ def run_table(args):
     dims = WORKLOAD["dims"]
     U = li.gauge(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(U, recon=args.recon)
+    wd.load_gauge(U, recon=args.recon, temporal_gauge=args.temporal_gauge)
     del U
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     fx = wd.new_field(wdp.F64, 2)
@@ -454,7 +481,61 @@ def run_table(args):
                                  "status": r.status})
             del fb
     wd.close()
-    print(json.dumps({"table": "24x24x24x64 eps=0.3 solver comparison, tol 1e-12", "rows": rows}))
+    print(json.dumps({"table": "24x24x24x64 eps=0.3 solver comparison, tol 1e-12",
+                      "temporal_gauge": args.temporal_gauge, "rows": rows}))
+    return 0
+
+
+def run_oracle_timing(args):
+    """The FP64 CPU oracle timed on this host's cores, all of them and one:
+    the dslash on 24^3x64 (and 64^3x128 with all cores) and full Schur
+    BiCGstab solves on 8^3x16 (tol 1e-12) and, by a bounded sample of
+    iterations scaled to the full iteration count, on 24^3x64."""
+    out = {"host_cores": os.cpu_count(), "runs": {}}
+    for threads in (os.cpu_count(), 1):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-timing-child", str(threads)]
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
+        out["runs"][str(threads)] = json.loads(r.stdout.strip().splitlines()[-1])
+    print(json.dumps(out))
+    return 0
+
+
+def run_oracle_timing_child(threads):
+    import oracle
+    import lattice_inputs as li
+    res = {"threads": threads}
+    dims = (8, 8, 8, 16)
+    U, b = li.gauge(dims, 0.5, 1000), li.gaussian_spinor(dims, 2000)
+    t0 = time.perf_counter()
+    _, st, iters, rel = oracle.solve(b, U, dims, 0.12, tol=1e-12)
+    res["solve_8x8x8x16"] = {"s": round(time.perf_counter() - t0, 3), "iters": iters, "true_rel_residual": rel}
+    dims = WORKLOAD["dims"]
+    U, b = li.gauge(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"]), li.gaussian_spinor(dims, WORKLOAD["source_seed"])
+    t0 = time.perf_counter()
+    oracle.dslash(b, U, dims, out_parity=0)
+    t = time.perf_counter() - t0
+    vh = li.volume(dims) // 2
+    res["dslash_24x24x24x64"] = {"s": round(t, 3), "ns_per_site": round(1e9 * t / vh, 1),
+                                 "gflops": round(1320 * vh / t / 1e9, 2)}
+    n = 10 if threads > 1 else 2
+    t0 = time.perf_counter()
+    oracle.bicgstab_schur_iterations(b, U, dims, WORKLOAD["kappa"], n)
+    s_it = (time.perf_counter() - t0) / n
+    full = oracle_iterations(WORKLOAD["kappa"])
+    res["solve_24x24x24x64"] = {"s_per_iteration": round(s_it, 3), "iterations": full,
+                                "s_est": round(s_it * full, 2), "sample_iterations": n}
+    if threads > 1:
+        del U, b
+        dims = (64, 64, 64, 128)
+        U, b = li.gauge(dims, 0.3, 1002), li.gaussian_spinor(dims, 2102)
+        t0 = time.perf_counter()
+        oracle.dslash(b, U, dims, out_parity=0)
+        t = time.perf_counter() - t0
+        vh = li.volume(dims) // 2
+        res["dslash_" + "x".join(map(str, dims))] = {"s": round(t, 3), "ns_per_site": round(1e9 * t / vh, 1),
+                                                     "gflops": round(1320 * vh / t / 1e9, 2)}
+    print(json.dumps(res))
     return 0
 
 
@@ -466,7 +547,8 @@ def run_dslash_only(args):
     dims = tuple(int(x) for x in args.sweep_dims.split(","))
     prec = wdp.PREC_BY_NAME[args.dslash_only]
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(li.gauge(dims, 0.3, 1002), recon=args.recon)
+    wd.load_gauge(li.gauge(dims, 0.3, 1002), recon=args.recon, temporal_gauge=args.temporal_gauge,
+                  recon8=args.recon8)
     fin = wd.upload(li.gaussian_spinor(dims, 2102), prec, parity=wdp.ODD)
     fout = wd.new_field(prec)
     for _ in range(args.warmup + args.steps):
@@ -482,8 +564,9 @@ def run_dslash_only(args):
         ts.append(e0.elapsed_time(e1) / 1000.0)
     t = statistics.mean(ts)
     vh = li.volume(dims) // 2
-    gbs = bytes_per_site(prec, args.recon) * vh / t / 1e9
-    print(json.dumps({"dslash": args.dslash_only, "lattice": "x".join(map(str, dims)), "us": round(t * 1e6, 2),
+    gbs = bytes_per_site(prec, args.recon, args.temporal_gauge, args.recon8) * vh / t / 1e9
+    print(json.dumps({"dslash": args.dslash_only, "lattice": "x".join(map(str, dims)),
+                      "temporal_gauge": args.temporal_gauge, "recon8": args.recon8, "us": round(t * 1e6, 2),
                       "GB/s": round(gbs, 1), "frac": round(gbs / peaks()[0], 4)}))
     return 0
 
@@ -502,7 +585,7 @@ def run_batch(args):
     kappas = [0.118, 0.12, 0.122, 0.124]
     inner = wdp.PREC_BY_NAME[args.inner]
     wd = wdp.WilsonDirac(dims)
-    wd.load_gauge(li.gauge(dims, 0.3, 1003), recon=args.recon)
+    wd.load_gauge(li.gauge(dims, 0.3, 1003), recon=args.recon, temporal_gauge=args.temporal_gauge)
     V = li.volume(dims)
     pts = [(s, c) for s in range(4) for c in range(3)]
     n = len(pts) * len(kappas)
@@ -603,6 +686,7 @@ def run_batch(args):
     mrhs["f64_single_x16_us"] = round(1e6 * statistics.mean(d64["single"]), 1)
     del f64in, f64out
     print(json.dumps({"batch": "32x32x32x64, 12 point sources x 4 kappa", "n_systems": n, "inner": args.inner,
+                      "temporal_gauge": args.temporal_gauge,
                       "mrhs_dslash": mrhs,
                       "fp64_link_reals": args.recon, "s_per_batched_solve": round(t_batch, 4),
                       "systems_per_s": round(n / t_batch, 3), "s_first_call_incl_tuning": round(first_s, 3),
@@ -635,7 +719,7 @@ def run_serve(args):
     tols = np.array([1e-8, 1e-10, 1e-12])[rng.integers(0, 3, size=n)]
     inner = wdp.PREC_BY_NAME[args.inner]
     srv = wdp.Server(budget_bytes=80 * 1000**3, max_slots=args.serve_slots, iters_per_step=args.serve_iters,
-                     inner_precision=inner, delta=0.1)
+                     inner_precision=inner, delta=0.1, temporal_gauge=args.temporal_gauge)
     gids, srcs, outs = {}, {}, {}
     t0 = time.perf_counter()
     for v, dims in enumerate(vols):
@@ -677,6 +761,7 @@ def run_serve(args):
             per_vol["x".join(map(str, dims))] = {"n": int(len(lv)), "p50_s": round(float(np.percentile(lv, 50)), 3),
                                                  "p99_s": round(float(np.percentile(lv, 99)), 3)}
     print(json.dumps({"serve": f"{n} Poisson requests at 200/s, 4 volumes, 8 resident gauge fields, budget 80 GB",
+                      "temporal_gauge": args.temporal_gauge,
                       "inner": args.inner, "requests": n, "converged_to_tol": ok, "makespan_s": round(makespan, 3),
                       "solves_per_s": round(n / makespan, 3),
                       "latency_p50_s": round(float(np.percentile(lat_a, 50)), 3),
@@ -699,6 +784,10 @@ def main():
     ap.add_argument("--no-sweep", dest="sweep", action="store_false")
     ap.add_argument("--sweep-dims", default="64,64,64,128")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--temporal-gauge", action=argparse.BooleanOptionalAction, default=True,
+                    help="load the links in the temporal gauge (Sec. 4.3; default on)")
+    ap.add_argument("--recon8", action=argparse.BooleanOptionalAction, default=False,
+                    help="FP32 / 16-bit links as the 8 numbers of App. A.2")
     ap.add_argument("--recon", type=int, default=18, choices=[12, 18],
                     help="reals stored per FP64 link (lower precisions always store 12)")
     ap.add_argument("--host-loop", action="store_true",
@@ -708,6 +797,9 @@ def main():
                     help="time only the dslash of one precision on --sweep-dims (profiling case)")
     ap.add_argument("--batch", action="store_true", help="batched 48-system multi-RHS solve (32^3x64)")
     ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="time the FP64 CPU oracle (dslash, solves) on all host cores and on one")
+    ap.add_argument("--oracle-timing-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--table", action="store_true",
                     help="solver comparison table on 24^3x64 (reliable update vs defect correction vs FP64)")
     ap.add_argument("--serve-requests", type=int, default=512)
@@ -720,6 +812,10 @@ def main():
         return run_serve(args)
     if args.table:
         return run_table(args)
+    if args.oracle_timing_child:
+        return run_oracle_timing_child(args.oracle_timing_child)
+    if args.oracle_timing:
+        return run_oracle_timing(args)
     if args.dslash_only:
         return run_dslash_only(args)
     if args.impl == "reference":

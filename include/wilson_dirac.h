@@ -24,7 +24,7 @@
  *   so that consecutive threads read consecutive 16-byte words:
  *     WD_F64 : 12 arrays of double2  (192 B/site)
  *     WD_F32 :  6 arrays of float4   ( 96 B/site)
- *     WD_Q16 :  3 arrays of 8 x int16 codes + 1 array of float norms (Sec. 4.5)
+ *     WD_Q16 :  3 arrays of 8 x int16 codes + 1 array of float norms (Sec. 4.6)
  *     WD_H16N:  3 arrays of 8 x fp16 + float norms
  *     WD_B16N:  3 arrays of 8 x bf16 + float norms       (52 B/site each)
  *   The byte size of one single-parity field is wd_field_bytes(ctx, prec).
@@ -102,8 +102,37 @@ size_t wd_field_bytes(const wd_ctx *ctx, wd_prec prec);
  * Replaces any previous gauge field. */
 wd_status wd_load_gauge(wd_ctx *ctx, const double *U, int is_device, int recon);
 
+/* Options of wd_load_gauge_opt (bitwise or). */
+typedef enum {
+  /* Sec. 4.3: load the links in the temporal gauge.  The library applies
+   * G(x, t) = U_4(x, 0) U_4(x, 1) ... U_4(x, t-1) (G = 1 on t = 0),
+   * U'_mu(x) = G(x) U_mu(x) G(x + mu)^dag; then every temporal link is the
+   * unit matrix except on the last time slice t = T-1 (where U'_4 is the
+   * product of U_4 around the time direction), and the dslash reads no
+   * temporal link and does no temporal SU(3) multiply away from that slice.
+   * Since D[U'] = G D[U] G^dag, the context's device fields hold G psi:
+   * wd_field_import applies G (after the App. B basis change) and
+   * wd_field_export applies G^dag, so every result seen through the host
+   * layout is that of the untransformed U (to the FP64 rounding of G, about
+   * 1e-15 relative).  G stays on the device (144 bytes per site, FP64). */
+  WD_GAUGE_TEMPORAL = 1,
+  /* App. A.2: the FP32 and 16-bit link copies hold 8 numbers per link
+   * {arg a1, arg c1, a2, a3, b1} instead of 12 reals, and the kernels rebuild
+   * the link from them (square roots and sine / cosine); the FP64 copy keeps
+   * `recon` reals.  Links with |a1| = 1 (the parametrisation's singularity,
+   * e.g. unit links) cannot be stored: the first use of a lower precision then
+   * fails with WD_ERR_INVALID_ARG (temporal links of WD_GAUGE_TEMPORAL off the
+   * last slice are never read and are exempt). */
+  WD_GAUGE_RECON8 = 2
+} wd_gauge_flags;
+
+/* wd_load_gauge with options (flags: wd_gauge_flags, 0 = wd_load_gauge).
+ * Device fields imported before this call belong to the previous gauge field
+ * and must be imported again. */
+wd_status wd_load_gauge_opt(wd_ctx *ctx, const double *U, int is_device, int recon, int flags);
+
 /* Host <-> device field transfer with reorder and precision conversion
- * (Sec. 4.1 layout; Sec. 4.5 16-bit storage; App. B: fields cross in the
+ * (Sec. 4.1 layout; Sec. 4.6 16-bit storage; App. B: fields cross in the
  * DeGrand-Rossi basis).  lex: V x 24 doubles, host (is_device = 0) or device.
  * Import reads the sites of `parity` from lex and writes the single-parity
  * device field `field`.  Export writes those sites of lex (others untouched). */
@@ -222,6 +251,7 @@ typedef struct {
   double delta;        /* reliable-update threshold (Alg. 2)                          */
   int max_iter;        /* per request                                                 */
   int use_graph;       /* 1: each step's iterations run as one CUDA graph             */
+  int gauge_flags;     /* wd_gauge_flags for every gauge field (wd_load_gauge_opt)    */
 } wd_server_params;
 
 wd_status wd_server_create(wd_server **out, const wd_server_params *params);

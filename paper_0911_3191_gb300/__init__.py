@@ -54,10 +54,17 @@ class SolveInfo(ctypes.Structure):
 class ServerParams(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("iters_per_step", ctypes.c_int),
                 ("inner_precision", ctypes.c_int), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("gauge_flags", ctypes.c_int)]
 
 
 _lib = None
+
+GAUGE_TEMPORAL, GAUGE_RECON8 = 1, 2
+
+
+def gauge_flags(temporal_gauge=False, recon8=False) -> int:
+    """wd_gauge_flags of wd_load_gauge_opt."""
+    return (GAUGE_TEMPORAL if temporal_gauge else 0) | (GAUGE_RECON8 if recon8 else 0)
 
 
 def library_path() -> str:
@@ -80,6 +87,7 @@ def load_library():
         "wd_set_stream": (c_int, [vp, vp]),
         "wd_field_bytes": (ctypes.c_size_t, [vp, c_int]),
         "wd_load_gauge": (c_int, [vp, vp, c_int, c_int]),
+        "wd_load_gauge_opt": (c_int, [vp, vp, c_int, c_int, c_int]),
         "wd_field_import": (c_int, [vp, vp, vp, c_int, c_int, c_int]),
         "wd_field_export": (c_int, [vp, vp, vp, c_int, c_int, c_int]),
         "wd_dslash": (c_int, [vp, vp, vp, c_int, c_int, c_int]),
@@ -115,6 +123,7 @@ def exported_symbols():
     """Names the C ABI exports (for load checks without a GPU)."""
     lib = load_library()
     return [n for n in ("wd_create", "wd_destroy", "wd_set_stream", "wd_field_bytes", "wd_load_gauge",
+                        "wd_load_gauge_opt",
                         "wd_field_import", "wd_field_export", "wd_dslash", "wd_dslash_xpay", "wd_apply_M", "wd_norm2",
                         "wd_solve", "wd_solve_device", "wd_dslash_batch", "wd_solve_batch", "wd_solve_batch_device",
                         "wd_server_create", "wd_server_destroy", "wd_server_add_gauge", "wd_server_submit",
@@ -195,11 +204,14 @@ class WilsonDirac:
         return self.torch.empty(nparity * self.field_bytes(prec), dtype=self.torch.uint8, device="cuda")
 
     # -- the C ABI, call for call
-    def load_gauge(self, U, recon: int = 12):
-        """U: (V, 4, 3, 3) complex128 numpy array, or an equivalent float64 CUDA tensor."""
+    def load_gauge(self, U, recon: int = 12, temporal_gauge: bool = False, recon8: bool = False):
+        """U: (V, 4, 3, 3) complex128 numpy array, or an equivalent float64 CUDA tensor.
+        temporal_gauge: the temporal gauge inside the library (Sec. 4.3);
+        recon8: FP32 / 16-bit links as the 8 numbers of App. A.2."""
         if isinstance(U, np.ndarray):
             U = np.ascontiguousarray(U, dtype=np.complex128)
-        self._check(self.lib.wd_load_gauge(self.ctx, ctypes.c_void_p(_ptr(U)), _is_device(U), recon), "load_gauge")
+        self._check(self.lib.wd_load_gauge_opt(self.ctx, ctypes.c_void_p(_ptr(U)), _is_device(U), recon,
+                                               gauge_flags(temporal_gauge, recon8)), "load_gauge")
 
     def field_import(self, field, lex, parity: int, prec: int):
         if isinstance(lex, np.ndarray):
@@ -327,13 +339,13 @@ class Server:
     fields, a device-memory budget, requests admitted as slots free up."""
 
     def __init__(self, budget_bytes=0, max_slots=8, iters_per_step=8, inner_precision=Q16, delta=0.1,
-                 max_iter=20000, use_graph=True):
+                 max_iter=20000, use_graph=True, temporal_gauge=False, recon8=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the Wilson-Dirac library runs on the GPU only")
         self.lib = load_library()
         p = ServerParams(int(budget_bytes), int(max_slots), int(iters_per_step), int(inner_precision), float(delta),
-                         int(max_iter), int(use_graph))
+                         int(max_iter), int(use_graph), gauge_flags(temporal_gauge, recon8))
         h = ctypes.c_void_p()
         st = self.lib.wd_server_create(ctypes.byref(h), ctypes.byref(p))
         if st != 0:

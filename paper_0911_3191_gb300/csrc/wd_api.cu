@@ -73,6 +73,99 @@ __global__ void gauge_pack_f64_kernel(Geom g, const double* lex, double2* out, i
   }
 }
 
+// ---- temporal gauge (Sec. 4.3), FP64 on the host-layout links in place.
+// 3x3 complex, row-major: c = a b, c = a b^dag.
+__device__ __forceinline__ void m3_mul(const double2* a, const double2* b, double2* c) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double re = 0.0, im = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double2 x = a[i * 3 + k], y = b[k * 3 + j];
+        re += x.x * y.x;
+        re -= x.y * y.y;
+        im += x.x * y.y;
+        im += x.y * y.x;
+      }
+      c[i * 3 + j] = make_double2(re, im);
+    }
+}
+__device__ __forceinline__ void m3_mul_dag(const double2* a, const double2* b, double2* c) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double re = 0.0, im = 0.0;
+      for (int k = 0; k < 3; ++k) {  // a_ik conj(b_jk)
+        const double2 x = a[i * 3 + k], y = b[j * 3 + k];
+        re += x.x * y.x;
+        re += x.y * y.y;
+        im += x.y * y.x;
+        im -= x.x * y.y;
+      }
+      c[i * 3 + j] = make_double2(re, im);
+    }
+}
+
+// G(x, 0) = 1, G(x, t + 1) = G(x, t) U_4(x, t): one thread per spatial site
+// walks the time direction.  G: [lexicographic site][9].
+__global__ void temporal_gauge_g_kernel(Geom g, const double* lex, double2* G) {
+  const long long ns = (long long)g.X * g.Y * g.Z;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < ns;
+       s += (long long)gridDim.x * blockDim.x) {
+    double2 m[9], n[9];
+    for (int k = 0; k < 9; ++k) m[k] = make_double2((k % 4 == 0) ? 1.0 : 0.0, 0.0);
+    for (int t = 0; t < g.T; ++t) {
+      const size_t site = (size_t)s + (size_t)ns * t;
+      for (int k = 0; k < 9; ++k) G[site * 9 + k] = m[k];
+      if (t + 1 < g.T) {
+        m3_mul(m, reinterpret_cast<const double2*>(lex + (site * 4 + 3) * 18), n);
+        for (int k = 0; k < 9; ++k) m[k] = n[k];
+      }
+    }
+  }
+}
+
+// U'_mu(x) = G(x) U_mu(x) G(x + mu)^dag: the temporal links become 1 except
+// on t = T-1, where U'_4 = G(x, T-1) U_4(x, T-1) (G(x, 0) = 1).
+__global__ void temporal_gauge_apply_kernel(Geom g, double* lex, const double2* G) {
+  const size_t V = (size_t)2 * g.Vh;
+  for (size_t site = blockIdx.x * (size_t)blockDim.x + threadIdx.x; site < V; site += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(site % g.X);
+    const int y = (int)((site / g.X) % g.Y);
+    const int z = (int)((site / ((size_t)g.X * g.Y)) % g.Z);
+    const int t = (int)(site / ((size_t)g.X * g.Y * g.Z));
+    const size_t step[3] = {1, (size_t)g.X, (size_t)g.X * g.Y};
+    const bool last[3] = {x == g.X - 1, y == g.Y - 1, z == g.Z - 1};
+    const size_t wrap[3] = {(size_t)(g.X - 1), (size_t)(g.Y - 1) * g.X, (size_t)(g.Z - 1) * g.X * g.Y};
+    const double2* gx = G + site * 9;
+    double2 tmp[9], out[9];
+    for (int mu = 0; mu < 3; ++mu) {
+      const size_t nb = last[mu] ? site - wrap[mu] : site + step[mu];
+      double2* u = reinterpret_cast<double2*>(lex + (site * 4 + mu) * 18);
+      m3_mul(gx, u, tmp);
+      m3_mul_dag(tmp, G + nb * 9, out);
+      for (int k = 0; k < 9; ++k) u[k] = out[k];
+    }
+    double2* u4 = reinterpret_cast<double2*>(lex + (site * 4 + 3) * 18);
+    if (t == g.T - 1) {
+      m3_mul(gx, u4, out);
+      for (int k = 0; k < 9; ++k) u4[k] = out[k];
+    } else {
+      for (int k = 0; k < 9; ++k) u4[k] = make_double2((k % 4 == 0) ? 1.0 : 0.0, 0.0);
+    }
+  }
+}
+
+// G (lexicographic) -> [parity][9][stride] at even-odd indices
+__global__ void temporal_gauge_pack_kernel(Geom g, const double2* G, double2* out) {
+  const int n = 2 * g.Vh;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int parity = i / g.Vh, h = i - parity * g.Vh;
+    int x, y, z, t;
+    site_coords(g, h, parity, x, y, z, t);
+    const size_t s = (size_t)x + (size_t)g.X * (y + (size_t)g.Y * (z + (size_t)g.Z * t));
+    for (int k = 0; k < 9; ++k) out[(size_t)(parity * 9 + k) * g.stride + h] = G[s * 9 + k];
+  }
+}
+
 // FP64 copy (first two rows) -> FP32 / 16-bit copies
 __global__ void gauge_f64_to_f32_kernel(Geom g, const double2* in, int nc, float4* out) {
   const int n = 8 * g.Vh;
@@ -236,6 +329,51 @@ int grid_for(const Ctx& c, int n, int block) {
   return b < cap ? b : cap;
 }
 
+// FP64 copy -> the 8 numbers of App. A.2 per link: {arg a1, arg c1, a2, a3,
+// b1}.  FP32: two float4 [p][mu][2][stride]; 16-bit: one uint4 [p][mu][stride],
+// the angles as fixed-point codes rint(32767 angle / pi) in every 16-bit
+// format, a2, a3, b1 in the format's own encoding.  Counts in *nsing
+// the links that the dslash reads and that sit at the parametrisation's
+// singularity |a1| = 1 (N = sqrt(|a2|^2 + |a3|^2) below 1e-6); temporal links
+// of the temporal gauge off the last slice are never read.
+template <int P>
+__global__ void gauge_f64_to_8_kernel(Geom g, const double2* in, int nc, void* out, unsigned* nsing) {
+  const int n = 8 * g.Vh;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int pm = i / g.Vh, h = i - pm * g.Vh;
+    const int parity = pm >> 2, mu = pm & 3;
+    double2 r[6];
+    for (int c = 0; c < 6; ++c) r[c] = in[((size_t)pm * nc + c) * g.stride + h];
+    double2 c1;
+    if (nc == 9) {
+      c1 = in[((size_t)pm * nc + 6) * g.stride + h];
+    } else {  // c1 = conj(a2 b3 - a3 b2)
+      const double re = r[1].x * r[5].x - r[1].y * r[5].y - (r[2].x * r[4].x - r[2].y * r[4].y);
+      const double im = r[1].x * r[5].y + r[1].y * r[5].x - (r[2].x * r[4].y + r[2].y * r[4].x);
+      c1 = make_double2(re, -im);
+    }
+    const double n2 = r[1].x * r[1].x + r[1].y * r[1].y + r[2].x * r[2].x + r[2].y * r[2].y;
+    int x, y, z, t;
+    site_coords(g, h, parity, x, y, z, t);
+    const bool read = !(g.tfix && mu == 3 && t != g.T - 1);
+    if (read && n2 < 1e-12) atomicAdd(nsing, 1u);
+    const double q[8] = {atan2(r[0].y, r[0].x), atan2(c1.y, c1.x), r[1].x, r[1].y, r[2].x, r[2].y, r[3].x, r[3].y};
+    if constexpr (P == WD_F32) {
+      float4* o = reinterpret_cast<float4*>(out);
+      o[((size_t)pm * 2) * g.stride + h] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+      o[((size_t)pm * 2 + 1) * g.stride + h] = make_float4((float)q[4], (float)q[5], (float)q[6], (float)q[7]);
+    } else {
+      constexpr Fmt16 F = (P == WD_Q16) ? Fmt16::Q16 : (P == WD_H16N) ? Fmt16::H16 : Fmt16::B16;
+      const double ip = 0.31830988618379067154;  // 1/pi
+      uint32_t w[4];
+      // the angles as 16-bit fixed point in every format, the rest in the format's own
+      w[0] = link16<Fmt16::Q16>(q[0] * ip) | (link16<Fmt16::Q16>(q[1] * ip) << 16);
+      for (int k = 1; k < 4; ++k) w[k] = link16<F>(q[2 * k]) | (link16<F>(q[2 * k + 1]) << 16);
+      reinterpret_cast<uint4*>(out)[(size_t)pm * g.stride + h] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 wd_status ensure_gauge(wd_ctx* ctx, int prec) {
   Ctx& c = ctx->c;
   if (!c.gauge_loaded) return set_err(ctx, WD_ERR_STATE, "no gauge field loaded (call wd_load_gauge first)");
@@ -245,6 +383,27 @@ wd_status ensure_gauge(wd_ctx* ctx, int prec) {
   const double2* src = (const double2*)c.gauge[WD_F64];
   const int grid = grid_for(c, 8 * c.g.Vh, 256);
   wd_status st;
+  if (c.low_recon == 8 && prec != WD_F64) {
+    const size_t bytes = links * (prec == WD_F32 ? 2 * sizeof(float4) : sizeof(uint4));
+    if ((st = dev_alloc(ctx, &c.gauge[prec], bytes)) != WD_OK) return st;
+    unsigned* nsing = reinterpret_cast<unsigned*>(c.scalars);
+    WD_CK(ctx, cudaMemsetAsync(nsing, 0, sizeof(unsigned), c.stream));
+    if (prec == WD_F32) gauge_f64_to_8_kernel<WD_F32><<<grid, 256, 0, c.stream>>>(c.g, src, nc, c.gauge[prec], nsing);
+    else if (prec == WD_Q16) gauge_f64_to_8_kernel<WD_Q16><<<grid, 256, 0, c.stream>>>(c.g, src, nc, c.gauge[prec], nsing);
+    else if (prec == WD_H16N) gauge_f64_to_8_kernel<WD_H16N><<<grid, 256, 0, c.stream>>>(c.g, src, nc, c.gauge[prec], nsing);
+    else gauge_f64_to_8_kernel<WD_B16N><<<grid, 256, 0, c.stream>>>(c.g, src, nc, c.gauge[prec], nsing);
+    WD_CK_LAUNCH(ctx, "gauge conversion (8 numbers)");
+    unsigned h_nsing = 0;
+    WD_CK(ctx, cudaMemcpyAsync(&h_nsing, nsing, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    WD_CK(ctx, cudaStreamSynchronize(c.stream));
+    if (h_nsing) {
+      dev_free(c.gauge[prec]);
+      return set_err(ctx, WD_ERR_INVALID_ARG,
+                     "8-number link storage: " + std::to_string(h_nsing) +
+                         " links have |a1| = 1 (the parametrisation's singularity, App. A.2)");
+    }
+    return WD_OK;
+  }
   if (prec == WD_F32) {
     if ((st = dev_alloc(ctx, &c.gauge[prec], links * 3 * sizeof(float4))) != WD_OK) return st;
     gauge_f64_to_f32_kernel<<<grid, 256, 0, c.stream>>>(c.g, src, nc, (float4*)c.gauge[prec]);
@@ -582,6 +741,7 @@ wd_status wd_create(wd_ctx** out, const int dims[4], int t_antiperiodic, void* c
   memcpy(c.dims, dims, sizeof(c.dims));
   c.stream = (cudaStream_t)cuda_stream;
   c.recon = 12;
+  c.low_recon = 12;
   c.sb_prec = c.sb_solver = -1;
   c.graph_prec = c.graph_solver = -1;
   wd_status st = WD_OK;
@@ -626,6 +786,7 @@ wd_status wd_destroy(wd_ctx* ctx) {
   dev_free((void*&)c.sb.ctl);
   dev_free(c.sb_full[0]);
   dev_free(c.sb_full[1]);
+  dev_free((void*&)c.gfix);
   batch_release(c);
   if (c.host_pinned) cudaFreeHost(c.host_pinned);
   delete ctx;
@@ -644,32 +805,58 @@ size_t wd_field_bytes(const wd_ctx* ctx, wd_prec prec) {
 }
 
 wd_status wd_load_gauge(wd_ctx* ctx, const double* U, int is_device, int recon) {
-  if (!ctx || !U || (recon != 12 && recon != 18)) return set_err(ctx, WD_ERR_INVALID_ARG, "wd_load_gauge: bad args");
+  return wd_load_gauge_opt(ctx, U, is_device, recon, 0);
+}
+
+wd_status wd_load_gauge_opt(wd_ctx* ctx, const double* U, int is_device, int recon, int flags) {
+  if (!ctx || !U || (recon != 12 && recon != 18) || (flags & ~(WD_GAUGE_TEMPORAL | WD_GAUGE_RECON8)))
+    return set_err(ctx, WD_ERR_INVALID_ARG, "wd_load_gauge: bad args");
+  const int temporal_gauge = (flags & WD_GAUGE_TEMPORAL) ? 1 : 0;
   Ctx& c = ctx->c;
   WD_CK(ctx, cudaSetDevice(c.device));
   WD_CK(ctx, cudaStreamSynchronize(c.stream));
   destroy_graph(c);
+  batch_release(c);
   for (int p = 0; p < 5; ++p) {
     dev_free(c.gauge[p]);
     dev_free(c.gauge4[p]);
   }
+  dev_free((void*&)c.gfix);
   c.gauge_loaded = false;
+  c.g.tfix = 0;
   const size_t lex_bytes = (size_t)2 * c.g.Vh * 72 * sizeof(double);
   const double* src = U;
   double* staging = nullptr;
-  wd_status st;
-  if (!is_device) {
+  double2* glex = nullptr;
+  wd_status st = WD_OK;
+  // the temporal gauge transforms the links in place: always on a copy
+  if (!is_device || temporal_gauge) {
     if ((st = dev_alloc(ctx, &staging, lex_bytes)) != WD_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(staging, U, lex_bytes, cudaMemcpyHostToDevice, c.stream);
+    cudaError_t e = cudaMemcpyAsync(staging, U, lex_bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    c.stream);
     if (e != cudaSuccess) {
       cudaFree(staging);
       return cuda_err(ctx, e, "gauge upload");
     }
     src = staging;
   }
+  if (temporal_gauge) {
+    const size_t gbytes = (size_t)2 * c.g.Vh * 9 * sizeof(double2);
+    st = dev_alloc(ctx, &glex, gbytes);
+    if (st == WD_OK) st = dev_alloc(ctx, &c.gfix, (size_t)2 * 9 * c.g.stride * sizeof(double2));
+    if (st == WD_OK) {
+      const long long ns = (long long)c.g.X * c.g.Y * c.g.Z;
+      temporal_gauge_g_kernel<<<grid_for(c, (int)ns, 128), 128, 0, c.stream>>>(c.g, staging, glex);
+      temporal_gauge_apply_kernel<<<grid_for(c, 2 * c.g.Vh, 128), 128, 0, c.stream>>>(c.g, staging, glex);
+      temporal_gauge_pack_kernel<<<grid_for(c, 2 * c.g.Vh, 256), 256, 0, c.stream>>>(c.g, glex, c.gfix);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = cuda_err(ctx, e, "temporal gauge");
+    }
+  }
   c.recon = recon;
+  c.low_recon = (flags & WD_GAUGE_RECON8) ? 8 : 12;
   const int nc = recon / 2;
-  st = dev_alloc(ctx, &c.gauge[WD_F64], (size_t)8 * nc * c.g.stride * sizeof(double2));
+  if (st == WD_OK) st = dev_alloc(ctx, &c.gauge[WD_F64], (size_t)8 * nc * c.g.stride * sizeof(double2));
   if (st == WD_OK) {
     gauge_pack_f64_kernel<<<grid_for(c, 2 * c.g.Vh, 256), 256, 0, c.stream>>>(c.g, src, (double2*)c.gauge[WD_F64],
                                                                                nc);
@@ -678,7 +865,13 @@ wd_status wd_load_gauge(wd_ctx* ctx, const double* U, int is_device, int recon) 
     if (e != cudaSuccess) st = cuda_err(ctx, e, "gauge pack");
   }
   if (staging) cudaFree(staging);
-  if (st == WD_OK) c.gauge_loaded = true;
+  if (glex) cudaFree(glex);
+  if (st == WD_OK) {
+    c.gauge_loaded = true;
+    c.g.tfix = temporal_gauge;
+  } else {
+    dev_free((void*&)c.gfix);
+  }
   return st;
 }
 

@@ -92,7 +92,8 @@ __device__ __forceinline__ void hop_tile(const In& in, const R* lk, int sx, int 
 
 // temporal hop from the tile: half-spinor load, diagonal projector
 template <bool FWD, bool DAGGER, typename R, class In>
-__device__ __forceinline__ void hop_tile_t(const In& in, const R* lk, int sx, int h_nbr, bool flip, R (&acc)[24]) {
+__device__ __forceinline__ void hop_tile_t(const In& in, const R* lk, int sx, int h_nbr, bool flip, bool unit,
+                                           R (&acc)[24]) {
   constexpr int S = (FWD != DAGGER) ? -1 : +1;
   constexpr bool upper = (S == +1);
   constexpr int which = 6 + (FWD ? 0 : 1);
@@ -106,6 +107,10 @@ __device__ __forceinline__ void hop_tile_t(const In& in, const R* lk, int sx, in
   } else {
     in.load_half(h_nbr, upper, hs);
   }
+  if (unit) {  // temporal gauge: the link is 1
+    accumulate_temporal<FWD, upper>(hs, acc, flip ? -(R)2 * w : (R)2 * w);
+    return;
+  }
   R u[18];
 #pragma unroll
   for (int k = 0; k < 18; ++k) u[k] = lk[(which * 18 + k) * 32 + sx];
@@ -116,7 +121,7 @@ __device__ __forceinline__ void hop_tile_t(const In& in, const R* lk, int sx, in
 
 template <bool DAGGER, typename R, class In>
 __device__ __forceinline__ void dslash_site_tile(const In& in, const R* lk, int sx, const int (&nb)[8], bool top,
-                                                 bool bot, R (&acc)[24]) {
+                                                 bool bot, bool unit_fwd, bool unit_bwd, R (&acc)[24]) {
 #pragma unroll
   for (int k = 0; k < 24; ++k) acc[k] = 0;
   hop_tile<0, true, DAGGER>(in, lk, sx, nb[0], false, acc);
@@ -125,8 +130,8 @@ __device__ __forceinline__ void dslash_site_tile(const In& in, const R* lk, int 
   hop_tile<1, false, DAGGER>(in, lk, sx, nb[3], false, acc);
   hop_tile<2, true, DAGGER>(in, lk, sx, nb[4], false, acc);
   hop_tile<2, false, DAGGER>(in, lk, sx, nb[5], false, acc);
-  hop_tile_t<true, DAGGER>(in, lk, sx, nb[6], top, acc);
-  hop_tile_t<false, DAGGER>(in, lk, sx, nb[7], bot, acc);
+  hop_tile_t<true, DAGGER>(in, lk, sx, nb[6], top, unit_fwd, acc);
+  hop_tile_t<false, DAGGER>(in, lk, sx, nb[7], bot, unit_bwd, acc);
 }
 
 template <typename R>
@@ -158,8 +163,11 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
         neighbours(g, hs, x, y, z, t, nb);
         const int mu = which >> 1;
         const bool fwd = (which & 1) == 0;
+        // temporal gauge: unit temporal links off the last slice are not read
+        if (g.tfix && mu == 3 && (fwd ? t != g.T - 1 : t != 0)) continue;
         R u[18];
-        gauge.load(fwd ? parity : 1 - parity, mu, fwd ? hs : nb[which], u);
+        if (gauge.recon == 8) gauge.template load<true>(fwd ? parity : 1 - parity, mu, fwd ? hs : nb[which], u);
+        else gauge.template load<false>(fwd ? parity : 1 - parity, mu, fwd ? hs : nb[which], u);
 #pragma unroll
         for (int k = 0; k < 18; ++k) lk[(which * 18 + k) * 32 + sx] = u[k];
       }
@@ -168,13 +176,15 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
     const int h = tile * 32 + threadIdx.x;
     const bool site_ok = h < g.Vh;
     int nb[8];
-    bool top = false, bot = false;
+    bool top = false, bot = false, unit_fwd = false, unit_bwd = false;
     if (site_ok) {
       int x, y, z, t;
       site_coords(g, h, parity, x, y, z, t);
       neighbours(g, h, x, y, z, t, nb);
       top = g.tbc_anti && (t == g.T - 1);
       bot = g.tbc_anti && (t == 0);
+      unit_fwd = g.tfix && (t != g.T - 1);
+      unit_bwd = g.tfix && (t != 0);
     }
     const int nwork = (ba.mode == 1 && ba.bc) ? *(const volatile int*)&ba.bc->nupd : ba.nrhs;
     for (int r0 = 0; r0 < nwork; r0 += TR) {
@@ -185,7 +195,7 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
       for (int k = 0; k < NR; ++k) red[k] = 0.0;
       if (site_ok && rhs_active(ba, r)) {
         R acc[24];
-        dslash_site_tile<DAGGER>(in.at(r), lk, threadIdx.x, nb, top, bot, acc);
+        dslash_site_tile<DAGGER>(in.at(r), lk, threadIdx.x, nb, top, bot, unit_fwd, unit_bwd, acc);
         epi.at(r)(h, acc, red);
       }
       if constexpr (Epi::NRED > 0) {

@@ -40,6 +40,7 @@ struct Geom {
   int Vh;      // sites of one parity
   int stride;  // elements between component arrays of a field (>= Vh)
   int tbc_anti;
+  int tfix;           // temporal gauge (Sec. 4.3): U_4 = 1 off the slice t = T-1
   int XhY, XhYZ;      // even-odd index steps in y, z (t step is XhYZ)
   int wy, wz, wt;     // index jumps of the periodic wrap in y, z, t
   FastDiv dXh, dY, dZ;
@@ -56,6 +57,7 @@ inline Geom make_geom(const int dims[4], int tbc_anti) {
   g.Vh = (int)vh;
   g.stride = (int)((vh + 31) / 32 * 32);
   g.tbc_anti = tbc_anti ? 1 : 0;
+  g.tfix = 0;
   g.XhY = g.Xh * g.Y;
   g.XhYZ = g.XhY * g.Z;
   g.wy = (g.Y - 1) * g.Xh;
@@ -198,7 +200,7 @@ struct SpinorF32 {
   static __device__ __forceinline__ float to_float(float f) { return f; }
 };
 
-// 16-bit formats with one FP32 norm per site (Sec. 4.5).  Codes: 3 x 16 B.
+// 16-bit formats with one FP32 norm per site (Sec. 4.6).  Codes: 3 x 16 B.
 enum class Fmt16 { Q16, H16, B16 };
 
 template <Fmt16 F>
@@ -305,7 +307,7 @@ struct Spinor16 {
   static __device__ __forceinline__ float f32(double d) { return __double2float_rn(d); }
   static __device__ __forceinline__ float f32(float f) { return f; }
 
-  // Encode 24 values (Sec. 4.5 format; FP32 arithmetic, see the header).
+  // Encode 24 values (Sec. 4.6 format; FP32 arithmetic, see the header).
   // v is replaced by the decoded values as stored.
   template <typename R>
   __device__ __forceinline__ void store_get(int h, R (&v)[24]) const {
@@ -371,6 +373,89 @@ __device__ __forceinline__ void reconstruct_row3(R (&u)[18]) {
   }
 }
 
+// App. A.2: the link from its 8 stored numbers p = {arg a1, arg c1, a2, a3,
+// b1} (complex a2, a3, b1 as re, im): |a1|^2 = 1 - |a2|^2 - |a3|^2 and
+// |c1|^2 = 1 - |a1|^2 - |b1|^2 = |a2|^2 + |a3|^2 - |b1|^2 (negative arguments
+// from rounding set to 0); with N^2 = |a2|^2 + |a3|^2 the unit vectors
+// b' = (0, -a3^*, a2^*)/N and c' = (a x b')^* = (N, -a1^* a2/N, -a1^* a3/N)
+// span the plane orthogonal to row a, and rows b, c are their SU(2) rotation
+// with p2 = b1/N, p1 = c1^*/N: b = p1 b' + p2 c', c = -p2^* b' + p1^* c'.
+// FAST: the SFU sine/cosine (16-bit storage, whose quantisation dominates).
+template <bool FAST>
+__device__ __forceinline__ void su3_from8(const float (&p)[8], float (&u)[18]) {
+  const float a2r = p[2], a2i = p[3], a3r = p[4], a3i = p[5], b1r = p[6], b1i = p[7];
+  float n2 = a2r * a2r;
+  n2 += a2i * a2i;
+  n2 += a3r * a3r;
+  n2 += a3i * a3i;
+  const float rn = rsqrtf(n2);  // 1/N
+  const float N = n2 * rn;
+  float b12 = b1r * b1r;
+  b12 += b1i * b1i;
+  const float a1m = sqrtf(fmaxf(0.f, 1.f - n2));
+  const float c1m = sqrtf(fmaxf(0.f, n2 - b12));
+  float sa, ca, sc, cc;
+  if constexpr (FAST) {
+    __sincosf(p[0], &sa, &ca);
+    __sincosf(p[1], &sc, &cc);
+  } else {
+    sincosf(p[0], &sa, &ca);
+    sincosf(p[1], &sc, &cc);
+  }
+  const float a1r = a1m * ca, a1i = a1m * sa;
+  const float c1r = c1m * cc, c1i = c1m * sc;
+  // p2 = b1 / N, p1 = conj(c1) / N
+  const float p2r = b1r * rn, p2i = b1i * rn;
+  const float p1r = c1r * rn, p1i = -c1i * rn;
+  // b' = (0, -conj(a3), conj(a2)) / N
+  const float bp1r = -a3r * rn, bp1i = a3i * rn;
+  const float bp2r = a2r * rn, bp2i = -a2i * rn;
+  // c' = (N, -conj(a1) a2 / N, -conj(a1) a3 / N)
+  float t;
+  t = a1r * a2r;
+  t += a1i * a2i;
+  const float cp1r = -t * rn;
+  t = a1r * a2i;
+  t -= a1i * a2r;
+  const float cp1i = -t * rn;
+  t = a1r * a3r;
+  t += a1i * a3i;
+  const float cp2r = -t * rn;
+  t = a1r * a3i;
+  t -= a1i * a3r;
+  const float cp2i = -t * rn;
+  u[0] = a1r; u[1] = a1i; u[2] = a2r; u[3] = a2i; u[4] = a3r; u[5] = a3i;
+  // row b: (b1, p1 b'_1 + p2 c'_1, p1 b'_2 + p2 c'_2)
+  u[6] = b1r; u[7] = b1i;
+  // row c: (c1, -conj(p2) b'_1 + conj(p1) c'_1, ...)
+  u[12] = c1r; u[13] = c1i;
+  const float bpr[2] = {bp1r, bp2r}, bpi[2] = {bp1i, bp2i}, cpr[2] = {cp1r, cp2r}, cpi[2] = {cp1i, cp2i};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    float re = p1r * bpr[j];
+    re -= p1i * bpi[j];
+    re += p2r * cpr[j];
+    re -= p2i * cpi[j];
+    float im = p1r * bpi[j];
+    im += p1i * bpr[j];
+    im += p2r * cpi[j];
+    im += p2i * cpr[j];
+    u[8 + 2 * j] = re;
+    u[9 + 2 * j] = im;
+    // -conj(p2) b' + conj(p1) c'
+    re = -p2r * bpr[j];
+    re -= p2i * bpi[j];
+    re += p1r * cpr[j];
+    re += p1i * cpi[j];
+    im = -p2r * bpi[j];
+    im += p2i * bpr[j];
+    im += p1r * cpi[j];
+    im -= p1i * cpr[j];
+    u[14 + 2 * j] = re;
+    u[15 + 2 * j] = im;
+  }
+}
+
 struct GaugeF64 {
   using real = double;
   static constexpr bool kScaled = false;
@@ -378,6 +463,11 @@ struct GaugeF64 {
   const double2* p;
   int stride;
   int recon;  // 12 or 18
+  template <bool R8, typename R>
+  __device__ __forceinline__ void load_scaled(int parity, int mu, int h, double (&u)[18], R&) const {
+    load<false>(parity, mu, h, u);
+  }
+  template <bool R8>
   __device__ __forceinline__ void load(int parity, int mu, int h, double (&u)[18]) const {
     const int nc = recon / 2;
     const double2* b = p + (size_t)(parity * 4 + mu) * nc * stride + h;
@@ -406,7 +496,22 @@ struct GaugeF32 {
   static constexpr float kScale = 1.f;
   const float4* p;
   int stride;
+  int recon;  // 12: rows a, b (3 float4 per link); 8: App. A.2 numbers (2 float4)
+  // R8: the kernel variant for recon == 8 (a compile-time choice, so the
+  // 12-real kernels carry none of the 8-number code)
+  template <bool R8, typename R>
+  __device__ __forceinline__ void load_scaled(int parity, int mu, int h, float (&u)[18], R&) const {
+    load<R8>(parity, mu, h, u);
+  }
+  template <bool R8>
   __device__ __forceinline__ void load(int parity, int mu, int h, float (&u)[18]) const {
+    if constexpr (R8) {
+      const float4* b = p + (size_t)(parity * 4 + mu) * 2 * stride + h;
+      const float4 d0 = __ldcs(b), d1 = __ldcs(b + stride);
+      const float q[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+      su3_from8<false>(q, u);
+      return;
+    }
     const float4* b = p + (size_t)(parity * 4 + mu) * 3 * stride + h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -428,9 +533,44 @@ struct Gauge16 {
   // accumulation.  fp16 / bf16 links hold U itself.
   static constexpr bool kScaled = (F == Fmt16::Q16);
   static constexpr float kScale = kInv32767;
-  const uint4* p8;  // [p][mu][stride]: reals 0..7
-  const uint2* p4;  // [p][mu][stride]: reals 8..11
+  const uint4* p8;  // [p][mu][stride]: reals 0..7 (recon 12) or the 8 numbers of App. A.2
+  const uint2* p4;  // [p][mu][stride]: reals 8..11 (recon 12)
   int stride;
+  int recon;  // 12 or 8
+  // App. A.2 numbers decoded to the link.  The two angles are 16-bit fixed
+  // point in every 16-bit format (code = rint(32767 angle / pi)); a2, a3, b1
+  // use the format's own encoding.
+  __device__ __forceinline__ void load8(int parity, int mu, int h, float (&u)[18]) const {
+    const uint4 a = __ldcs(p8 + (size_t)(parity * 4 + mu) * stride + h);
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+    constexpr float kPiQ = 3.14159265358979f * kInv32767;
+    float q[8];
+    q[0] = Spinor16<Fmt16::Q16>::lo(w[0]) * kPiQ;
+    q[1] = Spinor16<Fmt16::Q16>::hi(w[0]) * kPiQ;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      const float2 f = Spinor16<F>::pair(w[k]);
+      q[2 * k] = f.x;
+      q[2 * k + 1] = f.y;
+    }
+    if constexpr (F == Fmt16::Q16) {
+#pragma unroll
+      for (int k = 2; k < 8; ++k) q[k] *= kInv32767;
+    }
+    su3_from8<true>(q, u);
+  }
+  // the link values times 1/w' folded into w: Q16 12-real links come back as
+  // raw codes (w *= 1/32767), everything else as values.  R8: the kernel
+  // variant for recon == 8 (compile-time).
+  template <bool R8, typename R>
+  __device__ __forceinline__ void load_scaled(int parity, int mu, int h, float (&u)[18], R& w) const {
+    if constexpr (R8) {
+      load8(parity, mu, h, u);
+    } else {
+      load_raw(parity, mu, h, u);
+      if constexpr (F == Fmt16::Q16) w *= (R)kInv32767;
+    }
+  }
   __device__ __forceinline__ void load_raw(int parity, int mu, int h, float (&u)[18]) const {
     size_t o = (size_t)(parity * 4 + mu) * stride + h;
     uint4 a = __ldcs(p8 + o);
@@ -448,7 +588,12 @@ struct Gauge16 {
       for (int k = 12; k < 18; ++k) u[k] *= kInv32767;
     }
   }
+  template <bool R8>
   __device__ __forceinline__ void load(int parity, int mu, int h, float (&u)[18]) const {
+    if constexpr (R8) {
+      load8(parity, mu, h, u);
+      return;
+    }
     load_raw(parity, mu, h, u);
     if constexpr (F == Fmt16::Q16) {
 #pragma unroll
@@ -597,9 +742,11 @@ __device__ __forceinline__ void accumulate_temporal(const R (&g)[12], R (&a)[24]
   for (int k = 0; k < 12; ++k) a[o + k] += w2 * g[k];
 }
 
-template <bool FWD, bool DAGGER, typename R, class In, class G>
+// TFIX and off_slice: the link is the unit matrix (temporal gauge away from
+// the last time slice): no link load and no SU(3) multiply.
+template <bool FWD, bool DAGGER, bool TFIX, bool R8, typename R, class In, class G>
 __device__ __forceinline__ void hop_t(const In& in, const G& gauge, int parity, int h_link, int h_nbr, bool flip,
-                                      R (&acc)[24]) {
+                                      bool off_slice, R (&acc)[24]) {
   constexpr int S = (FWD != DAGGER) ? -1 : +1;
   constexpr bool upper = (S == +1);
   R hs[12];
@@ -612,19 +759,20 @@ __device__ __forceinline__ void hop_t(const In& in, const G& gauge, int parity, 
   } else {
     in.load_half(h_nbr, upper, hs);
   }
-  R u[18];
-  if constexpr (G::kScaled) {
-    gauge.load_raw(FWD ? parity : 1 - parity, 3, h_link, u);
-    w *= (R)G::kScale;
-  } else {
-    gauge.load(FWD ? parity : 1 - parity, 3, h_link, u);
+  if constexpr (TFIX) {
+    if (off_slice) {
+      accumulate_temporal<FWD, upper>(hs, acc, flip ? -(R)2 * w : (R)2 * w);
+      return;
+    }
   }
+  R u[18];
+  gauge.template load_scaled<R8>(FWD ? parity : 1 - parity, 3, h_link, u, w);
   R gs[12];
   su3_mul<!FWD>(u, hs, gs);
   accumulate_temporal<FWD, upper>(gs, acc, flip ? -(R)2 * w : (R)2 * w);
 }
 
-template <int MU, bool FWD, bool DAGGER, typename R, class In, class G>
+template <int MU, bool FWD, bool DAGGER, bool R8, typename R, class In, class G>
 __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, int h_link, int h_nbr, bool flip,
                                     R (&acc)[24]) {
   constexpr int S = (FWD != DAGGER) ? -1 : +1;
@@ -636,12 +784,7 @@ __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, in
   R hs[12];
   project<MU, S>(psi, hs);
   R u[18];
-  if constexpr (G::kScaled) {
-    gauge.load_raw(FWD ? parity : 1 - parity, MU, h_link, u);
-    w *= (R)G::kScale;
-  } else {
-    gauge.load(FWD ? parity : 1 - parity, MU, h_link, u);
-  }
+  gauge.template load_scaled<R8>(FWD ? parity : 1 - parity, MU, h_link, u, w);
   R gs[12];
   su3_mul<!FWD>(u, hs, gs);
   if constexpr (kScaled) {
@@ -659,7 +802,10 @@ __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, in
 // indices by offsets from h: in the even-odd order a step in y, z, t moves
 // the index by X/2, XY/2, XYZ/2; a step in x moves it by 0 or 1 depending on
 // the parity of x.
-template <bool DAGGER, typename R, class In, class G>
+// TFIX: the links are in the temporal gauge (g.tfix), so the temporal links
+// are 1 off the last time slice (a compile-time variant: the kernels for
+// general links carry no branch for it).
+template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G>
 __device__ __forceinline__ void dslash_site(const Geom& g, const In& in, const G& gauge, int h, int parity,
                                             R (&acc)[24]) {
   int x, y, z, t;
@@ -670,27 +816,27 @@ __device__ __forceinline__ void dslash_site(const Geom& g, const In& in, const G
     const int xo = x & 1;
     const int np = (x == g.X - 1) ? h - (g.Xh - 1) : h + xo;
     const int nm = (x == 0) ? h + (g.Xh - 1) : h - (xo ^ 1);
-    hop<0, true, DAGGER>(in, gauge, parity, h, np, false, acc);
-    hop<0, false, DAGGER>(in, gauge, parity, nm, nm, false, acc);
+    hop<0, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
+    hop<0, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
   }
   {
     const int np = (y == g.Y - 1) ? h - g.wy : h + g.Xh;
     const int nm = (y == 0) ? h + g.wy : h - g.Xh;
-    hop<1, true, DAGGER>(in, gauge, parity, h, np, false, acc);
-    hop<1, false, DAGGER>(in, gauge, parity, nm, nm, false, acc);
+    hop<1, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
+    hop<1, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
   }
   {
     const int np = (z == g.Z - 1) ? h - g.wz : h + g.XhY;
     const int nm = (z == 0) ? h + g.wz : h - g.XhY;
-    hop<2, true, DAGGER>(in, gauge, parity, h, np, false, acc);
-    hop<2, false, DAGGER>(in, gauge, parity, nm, nm, false, acc);
+    hop<2, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
+    hop<2, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
   }
   {
     const bool top = (t == g.T - 1), bot = (t == 0);
     const int np = top ? h - g.wt : h + g.XhYZ;
     const int nm = bot ? h + g.wt : h - g.XhYZ;
-    hop_t<true, DAGGER>(in, gauge, parity, h, np, top && g.tbc_anti, acc);
-    hop_t<false, DAGGER>(in, gauge, parity, nm, nm, bot && g.tbc_anti, acc);
+    hop_t<true, DAGGER, TFIX, R8>(in, gauge, parity, h, np, top && g.tbc_anti, !top, acc);
+    hop_t<false, DAGGER, TFIX, R8>(in, gauge, parity, nm, nm, bot && g.tbc_anti, !bot, acc);
   }
 }
 

@@ -110,10 +110,14 @@ struct Ctx {
   int device;
   int num_sms;
   // gauge copies (nullptr until loaded / derived)
-  int recon;
+  int recon;            // reals per FP64 link: 12 or 18
+  int low_recon;        // FP32 / 16-bit link storage: 12 reals or 8 numbers (App. A.2)
   void* gauge[5];       // by wd_prec: F64 double2; F32 float4; 16-bit: uint4 part
   void* gauge4[5];      // 16-bit: uint2 part
   bool gauge_loaded;
+  // temporal gauge (wd_load_gauge_opt): G(x) as [parity][9][stride] double2,
+  // or nullptr; c.g.tfix is set with it
+  double2* gfix;
   // reduction scratch
   RedScratch red;
   int max_red_blocks;

@@ -441,22 +441,30 @@ struct EpiRelupBicg {
       n += a[k] * a[k];
     }
     red[0] += n;
-    rh.store_get(h, a);
-    double wv[24];
+    // r_hat = r as stored in the inner precision; <r_tilde, r_hat> and
+    // |r_hat|^2 are inner-solver scalars: per-site partials in the inner
+    // precision's arithmetic (FP32 for FP32 and 16-bit storage), one FP64 add
+    // per site
+    using RI = typename RH::real;
+    RI q[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) q[k] = (RI)a[k];
+    rh.store_get(h, q);
+    RI wv[24];
     rt.load(h, wv);
-    double re = 0.0, im = 0.0, m = 0.0;
+    RI re = 0, im = 0, m = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      re += wv[2 * k] * a[2 * k];
-      re += wv[2 * k + 1] * a[2 * k + 1];
-      im += wv[2 * k] * a[2 * k + 1];
-      im -= wv[2 * k + 1] * a[2 * k];
-      m += a[2 * k] * a[2 * k];
-      m += a[2 * k + 1] * a[2 * k + 1];
+      re += wv[2 * k] * q[2 * k];
+      re += wv[2 * k + 1] * q[2 * k + 1];
+      im += wv[2 * k] * q[2 * k + 1];
+      im -= wv[2 * k + 1] * q[2 * k];
+      m += q[2 * k] * q[2 * k];
+      m += q[2 * k + 1] * q[2 * k + 1];
     }
-    red[1] += re;
-    red[2] += im;
-    red[3] += m;
+    red[1] += (double)re;
+    red[2] += (double)im;
+    red[3] += (double)m;
   }
 };
 
@@ -465,13 +473,18 @@ struct EpiRelupBicg {
 // ptxas register and spill counts): the FP32 and 16-bit kernels are
 // memory-latency bound and want warps, the fused-reduction epilogues need a
 // few more registers, and the FP64 kernel is bound by the FP64 pipe.
-template <typename R, class In, int NRED>
+template <typename R, class In, int NRED, bool TFIX, bool R8>
 struct DslashOccupancy {
-  static constexpr int kMinBlocks = (sizeof(R) == 8) ? 3 : In::kScaled ? (NRED == 0 ? 6 : 5) : (NRED == 0 ? 5 : 4);
+  static constexpr int kMinBlocks = (sizeof(R) == 8)       ? 3
+                                    : R8                  ? (NRED == 0 ? 4 : 3)
+                                    : In::kScaled         ? (TFIX ? (NRED == 0 ? 5 : 4) : (NRED == 0 ? 6 : 5))
+                                                          : (NRED == 0 ? 5 : 4);
 };
 
-template <bool DAGGER, typename R, class In, class G, class Epi>
-__global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRED>::kMinBlocks))
+// TFIX: links in the temporal gauge; R8: FP32 / 16-bit links as the 8
+// numbers of App. A.2.  Both are compile-time variants selected at launch.
+template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G, class Epi>
+__global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRED, TFIX, R8>::kMinBlocks))
     dslash_kernel(Geom g, In in, G gauge, int parity, Epi epi) {
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   double red[NR];
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
   for (int k = 0; k < NR; ++k) red[k] = 0.0;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
     R acc[24];
-    dslash_site<DAGGER>(g, in, gauge, h, parity, acc);
+    dslash_site<DAGGER, TFIX, R8>(g, in, gauge, h, parity, acc);
     epi(h, acc, red);
   }
   if constexpr (Epi::NRED > 0) grid_reduce<Epi::NRED>(red, epi.rs, epi.fin);
@@ -756,6 +769,44 @@ __device__ __forceinline__ void to_host_basis(const double (&v)[24], double (&d)
   }
 }
 
+// Temporal gauge (Sec. 4.3): colour rotation of every spin component of a
+// site by G(x) (import) or G(x)^dag (export).  G: [parity][9][stride]
+// double2, row-major 3x3.
+__device__ __forceinline__ void gauge_rotate(double (&v)[24], const double2* G, const Geom& g, int parity, int h,
+                                             bool dag) {
+  double2 m[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = G[(size_t)(parity * 9 + k) * g.stride + h];
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) {
+    double o[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double2 e = dag ? m[j * 3 + i] : m[i * 3 + j];
+        const double vr = v[(sp * 3 + j) * 2], vi = v[(sp * 3 + j) * 2 + 1];
+        if (dag) {  // conj(G_ji) v_j
+          re += e.x * vr;
+          re += e.y * vi;
+          im += e.x * vi;
+          im -= e.y * vr;
+        } else {  // G_ij v_j
+          re += e.x * vr;
+          re -= e.y * vi;
+          im += e.x * vi;
+          im += e.y * vr;
+        }
+      }
+      o[2 * i] = re;
+      o[2 * i + 1] = im;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[sp * 6 + k] = o[k];
+  }
+}
+
 // host layout (lexicographic FP64, [site][spin][colour][re,im]) <-> field
 template <class S>
 struct OpImport {
@@ -764,6 +815,7 @@ struct OpImport {
   S out;
   const double* lex;
   int parity;
+  const double2* gfix;  // temporal-gauge transformation, or nullptr
   __device__ __forceinline__ void operator()(int h, double*) const {
     int x, y, z, t;
     site_coords(g, h, parity, x, y, z, t);
@@ -777,6 +829,7 @@ struct OpImport {
       d[2 * k + 1] = e.y;
     }
     to_internal_basis(d, v);
+    if (gfix) gauge_rotate(v, gfix, g, parity, h, false);
     out.store(h, v);
   }
 };
@@ -788,6 +841,7 @@ struct OpExport {
   S in;
   double* lex;
   int parity;
+  const double2* gfix;
   __device__ __forceinline__ void operator()(int h, double*) const {
     using R = typename S::real;
     int x, y, z, t;
@@ -798,6 +852,7 @@ struct OpExport {
     double w[24], d[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) w[k] = (double)v[k];
+    if (gfix) gauge_rotate(w, gfix, g, parity, h, true);
     to_host_basis(w, d);
     double2* dst = reinterpret_cast<double2*>(lex + 24 * s);
 #pragma unroll
@@ -825,7 +880,7 @@ struct Tr<WD_F32> {
   using R = float;
   static size_t bytes(int stride) { return align256(96 * (size_t)stride); }
   static S view(const void* p, const Geom& g, size_t rs = 0) { return S{(float4*)p, g.stride, rs}; }
-  static G gauge(const Ctx& c) { return G{(const float4*)c.gauge[WD_F32], c.g.stride}; }
+  static G gauge(const Ctx& c) { return G{(const float4*)c.gauge[WD_F32], c.g.stride, c.low_recon}; }
 };
 template <Fmt16 F, int P>
 struct Tr16 {
@@ -836,7 +891,9 @@ struct Tr16 {
   static S view(const void* p, const Geom& g, size_t rs = 0) {
     return S{(uint4*)p, (float*)((char*)p + align256(48 * (size_t)g.stride)), g.stride, rs};
   }
-  static G gauge(const Ctx& c) { return G{(const uint4*)c.gauge[P], (const uint2*)c.gauge4[P], c.g.stride}; }
+  static G gauge(const Ctx& c) {
+    return G{(const uint4*)c.gauge[P], (const uint2*)c.gauge4[P], c.g.stride, c.low_recon};
+  }
 };
 template <>
 struct Tr<WD_Q16> : Tr16<Fmt16::Q16, WD_Q16> {};
@@ -859,10 +916,23 @@ template <typename R, class In, class G, class Epi>
 void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int dagger, const Epi& epi,
                    cudaStream_t s) {
   const int grid = dslash_grid(c);
-  if (dagger)
-    dslash_kernel<true, R, In, G, Epi><<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
-  else
-    dslash_kernel<false, R, In, G, Epi><<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
+  // FP64 links never use the 8 numbers
+  const bool r8 = (sizeof(R) == 4) && c.low_recon == 8;
+  auto go = [&](auto dag, auto tfix, auto rec8) {
+    dslash_kernel<decltype(dag)::value, decltype(tfix)::value, decltype(rec8)::value, R, In, G, Epi>
+        <<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
+  };
+  using T_ = std::true_type;
+  using F_ = std::false_type;
+  if constexpr (sizeof(R) == 4) {
+    if (r8) {
+      if (c.g.tfix) dagger ? go(T_{}, T_{}, T_{}) : go(F_{}, T_{}, T_{});
+      else dagger ? go(T_{}, F_{}, T_{}) : go(F_{}, F_{}, T_{});
+      return;
+    }
+  }
+  if (c.g.tfix) dagger ? go(T_{}, T_{}, F_{}) : go(F_{}, T_{}, F_{});
+  else dagger ? go(T_{}, F_{}, F_{}) : go(F_{}, F_{}, F_{});
 }
 
 template <class Op>
@@ -891,10 +961,10 @@ struct Impl {
     launch_dslash<R>(c, T::view(in, c.g), T::gauge(c), parity, dagger, e, s);
   }
   static void import_lex(const Ctx& c, void* field, const double* lex, int parity, cudaStream_t s) {
-    launch_sites(c, c.g.Vh, OpImport<S>{c.g, T::view(field, c.g), lex, parity}, s);
+    launch_sites(c, c.g.Vh, OpImport<S>{c.g, T::view(field, c.g), lex, parity, c.gfix}, s);
   }
   static void export_lex(const Ctx& c, double* lex, const void* field, int parity, cudaStream_t s) {
-    launch_sites(c, c.g.Vh, OpExport<S>{c.g, T::view(field, c.g), lex, parity}, s);
+    launch_sites(c, c.g.Vh, OpExport<S>{c.g, T::view(field, c.g), lex, parity, c.gfix}, s);
   }
   static void from_f64(const Ctx& c, void* out, const void* in, cudaStream_t s) {
     launch_sites(c, c.g.Vh, OpConvert<S, SpinorF64>{T::view(out, c.g), T64::view(in, c.g)}, s);

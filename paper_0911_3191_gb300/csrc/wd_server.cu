@@ -396,6 +396,7 @@ wd_status wd_server_create(wd_server** out, const wd_server_params* p) {
       p->inner_precision > WD_B16N || p->max_iter < 1)
     return WD_ERR_INVALID_ARG;
   if (p->inner_precision != WD_F64 && !(p->delta > 0.0 && p->delta < 1.0)) return WD_ERR_INVALID_ARG;
+  if (p->gauge_flags & ~(WD_GAUGE_TEMPORAL | WD_GAUGE_RECON8)) return WD_ERR_INVALID_ARG;
   wd_server* s = new (std::nothrow) wd_server();
   if (!s) return WD_ERR_OOM;
   s->p = *p;
@@ -442,12 +443,13 @@ wd_status wd_server_add_gauge(wd_server* s, const int dims[4], int t_antiperiodi
   if (ip == WD_F32) inner_gauge = links * 48;
   else if (ip != WD_F64) inner_gauge = links * 24;
   pl.fixed_bytes = links * (recon / 2) * 16 + inner_gauge + (size_t)2 * c.g.Vh * 24 * 8 + ((size_t)c.num_sms * 128 * 8);
+  if (s->p.gauge_flags & WD_GAUGE_TEMPORAL) pl.fixed_bytes += (size_t)2 * 9 * c.g.stride * 16;  // G (import / export)
   if (s->p.budget_bytes && s->used + pl.fixed_bytes > s->p.budget_bytes) {
     wd_destroy(pl.ctx);
     cudaStreamDestroy(st);
     return serr(s, WD_ERR_BUDGET, "gauge field does not fit the memory budget");
   }
-  r = wd_load_gauge(pl.ctx, U, 0, recon);
+  r = wd_load_gauge_opt(pl.ctx, U, 0, recon, s->p.gauge_flags);
   if (r == WD_OK) r = wd_internal_ensure_gauge(pl.ctx, ip);
   if (r != WD_OK) {
     std::string m = wd_last_error(pl.ctx);

@@ -3,7 +3,7 @@ the FP64 CPU oracle, through the C ABI (arXiv:0911.3191 Sec. 3-4, App. A-B).
 
 Bars: relative L2 error <= 1e-13 (FP64), 1e-6 (FP32), 5e-3 (16-bit storage)
 against the oracle on unquantised FP64 inputs; bit-exact codes and norms for
-the 16-bit codecs (Sec. 4.5)."""
+the 16-bit codecs (Sec. 4.6)."""
 import numpy as np
 import pytest
 
@@ -166,7 +166,7 @@ def test_free_field_plane_wave(wdp):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_accuracy_distribution_delta(wdp, prec):
-    """Delta(eps) of Sec. 4.6: the fraction of M_hat output components that
+    """Delta(eps) of Sec. 4.7: the fraction of M_hat output components that
     deviate from the CPU result by >= eps, for uniform eta in [0,1] and
     random SU(3) links; zero beyond the precision's accuracy, one well below."""
     dims = (8, 8, 8, 8)
