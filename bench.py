@@ -714,6 +714,8 @@ def run_serve(args):
     gaps = rng.exponential(1.0 / 200.0, size=n)
     arrival = np.cumsum(gaps) - gaps[0]
     vol_idx = rng.integers(0, 4, size=n)
+    allowed = [int(v) for v in args.serve_volumes.split(",")]
+    vol_idx = np.array([allowed[int(v) % len(allowed)] for v in vol_idx])
     field_idx = rng.integers(0, 2, size=n)
     kappas = rng.uniform(0.115, 0.124, size=n)
     tols = np.array([1e-8, 1e-10, 1e-12])[rng.integers(0, 3, size=n)]
@@ -729,6 +731,7 @@ def run_serve(args):
         outs[v] = np.zeros_like(srcs[v])
     setup_s = time.perf_counter() - t0
     pending, lat, infos = {}, [], []
+    t_step = t_poll = 0.0
     nxt = 0
     start = time.perf_counter()
     with ClockSampler(0) as clk:
@@ -743,16 +746,43 @@ def run_serve(args):
             if not pending:
                 time.sleep(max(0.0, min(arrival[nxt] - now, 0.01)))
                 continue
+            t_a = time.perf_counter()
             srv.step()
             tnow = time.perf_counter() - start
+            t_step += time.perf_counter() - t_a
+            t_a = time.perf_counter()
             for rid in list(pending):
                 f, res, _ = srv.poll(rid)
                 if f:
                     i, tol = pending.pop(rid)
                     lat.append(tnow - arrival[i])
                     infos.append((res, tol, int(vol_idx[i])))
+            t_poll += time.perf_counter() - t_a
     makespan = time.perf_counter() - start
+    server_stats = srv.stats()
+    srv.close()
+    # the same work done one solve at a time, inputs resident: one timed solo
+    # solve per (volume, tol) at the middle kappa 0.1195, summed over the requests
+    import torch
+    solo = {}
+    for v, dims in enumerate(vols):
+        wd = wdp.WilsonDirac(dims)
+        wd.load_gauge(li.gauge(dims, 0.3, 1100 + 2 * v), recon=args.recon, temporal_gauge=args.temporal_gauge)
+        fb = wd.upload(srcs[v], wdp.F64)
+        fx = wd.new_field(wdp.F64, 2)
+        for tol in (1e-8, 1e-10, 1e-12):
+            wd.solve_device(fx, fb, 0.1195, tol=tol, inner_precision=inner)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            wd.solve_device(fx, fb, 0.1195, tol=tol, inner_precision=inner)
+            torch.cuda.synchronize()
+            solo[(v, tol)] = time.perf_counter() - t1
+        wd.close()
+    serial = sum(solo[(int(vol_idx[i]), float(tols[i]))] for i in range(n))
     ok = sum(1 for r, tol, _ in infos if r.status == 0 and r.true_rel_residual <= tol)
+    failures = [{"status": r.status, "true_rel_residual": r.true_rel_residual, "tol": tol, "iters": r.iters,
+                 "volume": "x".join(map(str, vols[v]))}
+                for r, tol, v in infos if not (r.status == 0 and r.true_rel_residual <= tol)]
     lat_a = np.array(lat)
     per_vol = {}
     for v, dims in enumerate(vols):
@@ -767,8 +797,11 @@ def run_serve(args):
                       "latency_p50_s": round(float(np.percentile(lat_a, 50)), 3),
                       "latency_p99_s": round(float(np.percentile(lat_a, 99)), 3), "per_volume": per_vol,
                       "setup_s": round(setup_s, 1), "max_slots": args.serve_slots, "iters_per_step": args.serve_iters,
+                      "one_at_a_time_s": round(serial, 2), "efficiency_vs_one_at_a_time": round(serial / makespan, 3),
+                      "server_stats": server_stats, "host_step_s": round(t_step, 2), "host_poll_s": round(t_poll, 2),
+                      "failures": failures[:10],
+                      "solo_s": {f"{'x'.join(map(str, vols[v]))} tol {t:g}": round(x, 4) for (v, t), x in solo.items()},
                       "clocks": clk.summary()}))
-    srv.close()
     return 0
 
 
@@ -805,6 +838,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-iters", type=int, default=8)
+    ap.add_argument("--serve-volumes", default="0,1,2,3",
+                    help="which of the four volumes (16^3x32, 24^3x48, 32^3x64, 48^3x96) requests go to")
     args = ap.parse_args()
     if args.batch:
         return run_batch(args)

@@ -265,8 +265,11 @@ wd_status wd_server_add_gauge(wd_server *server, const int dims[4], int t_antipe
 
 /* Queue M_kappa x = b to |b - M x| <= tol |b| on gauge field gauge_id.  b and
  * x are host FP64 fields in the host layout that the caller keeps alive until
- * the request has finished; x is written when it finishes.  WD_ERR_BUDGET if
- * even one slot for this lattice can never fit the budget. */
+ * the request has finished; x is written when it finishes.  The server
+ * page-locks b and x (cudaHostRegister; buffers already page-locked are used
+ * as they are) so that their transfers overlap other work, and releases them
+ * when no unfinished request uses them.  WD_ERR_BUDGET if even one slot for
+ * this lattice can never fit the budget. */
 wd_status wd_server_submit(wd_server *server, int gauge_id, const double *b, double *x, double kappa, double tol,
                            long long *request_id);
 
@@ -283,6 +286,18 @@ wd_status wd_server_poll(wd_server *server, long long request_id, int *finished,
 
 /* Device bytes currently charged against the budget. */
 size_t wd_server_memory_in_use(const wd_server *server);
+
+/* Counters of a server since its creation: host seconds spent admitting
+ * requests (source upload, Schur source, slot setup), retiring them (FP64
+ * reconstruction, true residual, solution download) and waiting for a step
+ * when no pool could progress; device seconds of the pools' steps (summed
+ * over pools, which run concurrently); steps launched; requests admitted /
+ * retired. */
+typedef struct {
+  double admit_seconds, retire_seconds, wait_seconds, gpu_step_seconds;
+  long long steps, admitted, retired;
+} wd_server_stats;
+wd_status wd_server_get_stats(const wd_server *server, wd_server_stats *out);
 const char *wd_server_last_error(const wd_server *server);
 
 /* |field|^2 of one single-parity device field, in FP64, for callers that

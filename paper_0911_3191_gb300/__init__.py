@@ -51,6 +51,12 @@ class SolveInfo(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("admit_seconds", ctypes.c_double), ("retire_seconds", ctypes.c_double),
+                ("wait_seconds", ctypes.c_double), ("gpu_step_seconds", ctypes.c_double),
+                ("steps", ctypes.c_longlong), ("admitted", ctypes.c_longlong), ("retired", ctypes.c_longlong)]
+
+
 class ServerParams(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("iters_per_step", ctypes.c_int),
                 ("inner_precision", ctypes.c_int), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
@@ -108,6 +114,7 @@ def load_library():
         "wd_server_step": (c_int, [vp, ip, ip]),
         "wd_server_poll": (c_int, [vp, ctypes.c_longlong, ip, ctypes.POINTER(SolveInfo)]),
         "wd_server_memory_in_use": (ctypes.c_size_t, [vp]),
+        "wd_server_get_stats": (c_int, [vp, ctypes.POINTER(ServerStats)]),
         "wd_server_last_error": (ctypes.c_char_p, [vp]),
         "wd_last_error": (ctypes.c_char_p, [vp]),
         "wd_status_string": (ctypes.c_char_p, [c_int]),
@@ -128,6 +135,7 @@ def exported_symbols():
                         "wd_solve", "wd_solve_device", "wd_dslash_batch", "wd_solve_batch", "wd_solve_batch_device",
                         "wd_server_create", "wd_server_destroy", "wd_server_add_gauge", "wd_server_submit",
                         "wd_server_step", "wd_server_poll", "wd_server_memory_in_use", "wd_server_last_error",
+                        "wd_server_get_stats",
                         "wd_norm2_noalloc", "wd_last_error", "wd_status_string")
             if hasattr(lib, n)]
 
@@ -385,6 +393,11 @@ class Server:
                                               ctypes.byref(rid)), "submit")
         self._keep[rid.value] = (b, x)
         return rid.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._check(self.lib.wd_server_get_stats(self.h, ctypes.byref(st)), "stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
 
     def step(self):
         a, q = ctypes.c_int(), ctypes.c_int()

@@ -686,6 +686,22 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
 
 }  // namespace
 
+// both parities of a device FP64 field -> host lexicographic array, one
+// device-to-host copy, stream-ordered and not waited for (asynchronous when
+// the host array is page-locked)
+wd_status wd_internal_export_full_async(wd_ctx* ctx, double* host, const void* even, const void* odd) {
+  Ctx& c = ctx->c;
+  wd_status st = ensure_staging(ctx);
+  if (st != WD_OK) return st;
+  const PrecOps* o = ops_f64();
+  o->export_lex(c, c.lex_staging, even, 0, c.stream);
+  o->export_lex(c, c.lex_staging, odd, 1, c.stream);
+  WD_CK_LAUNCH(ctx, "export");
+  WD_CK(ctx, cudaMemcpyAsync(host, c.lex_staging, (size_t)2 * c.g.Vh * 24 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c.stream));
+  return WD_OK;
+}
+
 wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, const void* odd) {
   Ctx& c = ctx->c;
   wd_status st = ensure_staging(ctx);
@@ -697,6 +713,21 @@ wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, c
   WD_CK(ctx, cudaMemcpyAsync(host, c.lex_staging, (size_t)2 * c.g.Vh * 24 * sizeof(double), cudaMemcpyDeviceToHost,
                              c.stream));
   WD_CK(ctx, cudaStreamSynchronize(c.stream));
+  return WD_OK;
+}
+
+// host lexicographic FP64 field -> both parities of a device FP64 field, one
+// host-to-device copy; stream-ordered, returns once the host array may be reused
+wd_status wd_internal_import_full(wd_ctx* ctx, void* even, void* odd, const double* host) {
+  Ctx& c = ctx->c;
+  wd_status st = ensure_staging(ctx);
+  if (st != WD_OK) return st;
+  WD_CK(ctx, cudaMemcpyAsync(c.lex_staging, host, (size_t)2 * c.g.Vh * 24 * sizeof(double), cudaMemcpyHostToDevice,
+                             c.stream));
+  const PrecOps* o = ops_f64();
+  o->import_lex(c, even, c.lex_staging, 0, c.stream);
+  o->import_lex(c, odd, c.lex_staging, 1, c.stream);
+  WD_CK_LAUNCH(ctx, "import");
   return WD_OK;
 }
 

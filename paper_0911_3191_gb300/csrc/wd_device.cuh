@@ -240,6 +240,12 @@ struct Spinor16 {
     if constexpr (F == Fmt16::H16) {
       __half2 h = *reinterpret_cast<__half2*>(&w);
       return __half22float2(h);
+    } else if constexpr (F == Fmt16::Q16) {
+      // both codes to offset binary with one XOR, each placed under the
+      // exponent of 2^23 with one byte permute, then one subtraction each
+      const uint32_t x = w ^ 0x80008000u;
+      return make_float2(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8421376.0f,
+                         __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8421376.0f);
     } else {
       return make_float2(lo(w), hi(w));
     }

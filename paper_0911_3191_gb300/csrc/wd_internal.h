@@ -166,3 +166,5 @@ struct wd_ctx {
 wd_status wd_internal_ensure_gauge(wd_ctx* ctx, int prec);
 // host FP64 field (host layout) <- two single-parity FP64 device fields
 wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, const void* odd);
+wd_status wd_internal_import_full(wd_ctx* ctx, void* even, void* odd, const double* host);
+wd_status wd_internal_export_full_async(wd_ctx* ctx, double* host, const void* even, const void* odd);

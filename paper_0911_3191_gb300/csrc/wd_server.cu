@@ -21,6 +21,7 @@
 #include <deque>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "wd_batch.cuh"
@@ -35,10 +36,13 @@ struct Request {
   const double* b;
   double* x;
   double kappa, tol;
-  int state;  // 0 queued, 1 active, 2 finished
+  int state;  // 0 queued, 1 active, 3 solution download in flight, 2 finished
   int slot;
   wd_solve_info info;
   std::chrono::steady_clock::time_point t_submit;
+  SolverCtl final_ctl;           // the slot's control block when it retired
+  int scal_idx = -1;             // entry of wd_server::scal_pinned with its four norms
+  cudaEvent_t done_ev = nullptr; // recorded after the solution download
 };
 
 struct Pool {
@@ -60,18 +64,35 @@ struct Pool {
   SolverCtl* hctl = nullptr;        // pinned mirror of the ctl array
   double* hscal = nullptr;          // pinned mirror of per-slot scalars
   bool launched = false;            // a step of iterations is in flight
-  cudaEvent_t done_ev = nullptr;    // recorded after the step's iterations
+  cudaEvent_t start_ev = nullptr;   // recorded before the step's iterations
+  cudaEvent_t done_ev = nullptr;    // recorded after them
 };
 
 }  // namespace
+
+// A caller's host buffer, page-locked by the server (cudaHostRegister) so
+// that uploads and downloads run asynchronously; released when no pending
+// request uses it.  Buffers the caller had already page-locked are used as
+// they are.
+struct Pin {
+  size_t bytes = 0;
+  int refs = 0;
+  bool registered = false;
+};
 
 struct wd_server {
   wd_server_params p;
   std::vector<Pool> pools;
   std::map<long long, Request> reqs;
+  std::map<const void*, Pin> pins;
+  // pinned host entries (4 doubles: |b_e|^2, |b_o|^2, |r_e|^2, |r_o|^2) that
+  // retired requests' norms are downloaded into; free list of entries
+  double* scal_pinned = nullptr;
+  std::vector<int> scal_free;
   size_t used = 0;
   long long next_id = 1;
   std::string err;
+  wd_server_stats st{};
 };
 
 namespace {
@@ -79,6 +100,25 @@ namespace {
 wd_status serr(wd_server* s, wd_status st, const std::string& m) {
   if (s) s->err = m;
   return st;
+}
+
+void pin(wd_server* s, const void* p, size_t bytes) {
+  Pin& pn = s->pins[p];
+  if (pn.refs++ > 0) return;
+  pn.bytes = bytes;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost) return;  // already pinned
+  cudaGetLastError();
+  pn.registered = cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterDefault) == cudaSuccess;
+  if (!pn.registered) cudaGetLastError();  // pageable: transfers stay correct, just synchronous
+}
+
+void unpin(wd_server* s, const void* p) {
+  auto it = s->pins.find(p);
+  if (it == s->pins.end()) return;
+  if (--it->second.refs > 0) return;
+  if (it->second.registered) cudaHostUnregister(const_cast<void*>(p));
+  s->pins.erase(it);
 }
 
 #define WS_CK(s, call)                                                                                    \
@@ -101,8 +141,24 @@ int blas_gx_for(const Ctx& c, int n) {
   return std::max(1, std::min(per, need));
 }
 
+// launch shape for a capacity of n slots: right-hand sides per block no more
+// than the slots (a block's threads for absent systems idle), and enough
+// blocks that the sites of one system alone fill the device
+BatchLaunch pool_shape(const Ctx& c, int n) {
+  const int ntiles = (c.g.Vh + 31) / 32;
+  int tr = 1;
+  while (tr < n && tr < 4) tr *= 2;
+  int tr64 = 1;
+  while (tr64 < n && tr64 < 8) tr64 *= 2;
+  BatchLaunch bl{n, tr, std::min(c.num_sms * (64 / tr), ntiles), blas_gx_for(c, n)};
+  bl.tr64 = tr64;
+  bl.grid64 = std::min(c.num_sms * (32 / tr64), ntiles);
+  return bl;
+}
+
 size_t small_bytes(const Ctx& c, int n) {
-  const int maxblk = std::max(c.num_sms * 16, blas_gx_for(c, n));
+  const BatchLaunch bl = pool_shape(c, n);
+  const int maxblk = std::max(std::max(bl.grid, bl.grid64), bl.blas_gx);
   return align256((size_t)n * sizeof(SolverCtl)) + align256(sizeof(BatchCtl)) +
          align256((size_t)maxblk * n * 4 * sizeof(double)) + align256((size_t)2 * n * 8) + align256((size_t)4 * n * 8);
 }
@@ -197,7 +253,10 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
   b.bc = (BatchCtl*)s;
   s += align256(sizeof(BatchCtl));
   b.partials = (double*)s;
-  s += align256((size_t)std::max(c.num_sms * 16, blas_gx_for(c, cap)) * cap * 4 * sizeof(double));
+  {
+    const BatchLaunch bl = pool_shape(c, cap);
+    s += align256((size_t)std::max(std::max(bl.grid, bl.grid64), bl.blas_gx) * cap * 4 * sizeof(double));
+  }
   b.kappas = (double*)s;
   s += align256((size_t)2 * cap * 8);
   b.scal = (double*)s;
@@ -213,10 +272,7 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
   b.t = p; p += fin * cap;
   b.x_hat = p; p += fin * cap;
   b.tmp = p; p += fin * cap;
-  const int ntiles = (c.g.Vh + 31) / 32;
-  pl.bl = BatchLaunch{cap, 4, std::min(c.num_sms * 4, ntiles), blas_gx_for(c, cap)};
-  pl.bl.tr64 = 8;
-  pl.bl.grid64 = std::min(c.num_sms * 4, ntiles);
+  pl.bl = pool_shape(c, cap);
   mark_free_kernel<<<(cap + 127) / 128, 128, 0, c.stream>>>(b.ctl, cap);
   WS_CK(sv, cudaGetLastError());
   if (sv->p.use_graph) {
@@ -249,13 +305,22 @@ SolveBufs slot_bufs(Pool& pl, int r, int prec) {
 
 // admission of one request into slot r: source upload, Schur source, control
 // block, quantised residual; the other slots keep their Krylov state
+using Clock = std::chrono::steady_clock;
+double since(Clock::time_point t0) { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
 wd_status admit(wd_server* sv, Pool& pl, Request& q, int r) {
+  const auto t0 = Clock::now();
+  ++sv->st.admitted;
+  struct Acc {
+    wd_server* s;
+    Clock::time_point t;
+    ~Acc() { s->st.admit_seconds += since(t); }
+  } acc{sv, t0};
   Ctx& c = pl.ctx->c;
   const int prec = sv->p.inner_precision;
   const size_t f64 = fbytes(c, WD_F64);
   char* bf = (char*)pl.bfull + 2 * f64 * r;
-  wd_status st = wd_field_import(pl.ctx, bf, q.b, 0, WD_EVEN, WD_F64);
-  if (st == WD_OK) st = wd_field_import(pl.ctx, bf + f64, q.b, 0, WD_ODD, WD_F64);
+  wd_status st = wd_internal_import_full(pl.ctx, bf, bf + f64, q.b);
   if (st != WD_OK) return serr(sv, st, std::string("source upload: ") + wd_last_error(pl.ctx));
   const PrecOps* o64 = ops_f64();
   SolveBufs s = slot_bufs(pl, r, prec);
@@ -274,9 +339,19 @@ wd_status admit(wd_server* sv, Pool& pl, Request& q, int r) {
   return WD_OK;
 }
 
+wd_status finish(wd_server* sv, Request& q);
+
 // retirement of slot r: x_e, x_o = b_o + kappa D_oe x_e, the full FP64 true
-// residual, and the solution copied to the caller's host buffer
+// residual, and the solution downloaded to the caller's buffer; all stream
+// ordered (the slot can take a new request at once).  The request finishes
+// when its event, recorded after the download, has completed (finish()).
 wd_status retire(wd_server* sv, Pool& pl, Request& q, int r, const SolverCtl& hc) {
+  ++sv->st.retired;
+  struct Acc {
+    wd_server* s;
+    Clock::time_point t;
+    ~Acc() { s->st.retire_seconds += since(t); }
+  } acc{sv, Clock::now()};
   Ctx& c = pl.ctx->c;
   const int prec = sv->p.inner_precision;
   const size_t f64 = fbytes(c, WD_F64);
@@ -294,11 +369,40 @@ wd_status retire(wd_server* sv, Pool& pl, Request& q, int r, const SolverCtl& hc
                                                          T64::view(s.tmp64, g), ck, c.red, FinStore{sc + 3, 1}};
   launch_dslash<double>(c, T64::view(s.x, g), T64::gauge(c), 1, 0, eo, c.stream);
   WS_CK(sv, cudaGetLastError());
-  WS_CK(sv, cudaMemcpyAsync(pl.hscal + 4 * r, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-  // export both parities of x, then one copy to the caller
-  const wd_status st = wd_internal_export_full(pl.ctx, q.x, s.x, s.tmp64);
+  // the request's four norms into its own pinned entry
+  if (!sv->scal_pinned) {
+    constexpr int kEntries = 4096;
+    WS_CK(sv, cudaMallocHost((void**)&sv->scal_pinned, (size_t)kEntries * 4 * sizeof(double)));
+    for (int k = kEntries - 1; k >= 0; --k) sv->scal_free.push_back(k);
+  }
+  if (sv->scal_free.empty()) {  // more downloads in flight than entries: wait for them
+    WS_CK(sv, cudaDeviceSynchronize());
+    for (auto& kv : sv->reqs)
+      if (kv.second.state == 3) finish(sv, kv.second);
+  }
+  q.scal_idx = sv->scal_free.back();
+  sv->scal_free.pop_back();
+  WS_CK(sv, cudaMemcpyAsync(sv->scal_pinned + 4 * q.scal_idx, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                            c.stream));
+  const wd_status st = wd_internal_export_full_async(pl.ctx, q.x, s.x, s.tmp64);
   if (st != WD_OK) return serr(sv, st, std::string("solution download: ") + wd_last_error(pl.ctx));
-  const double* h = pl.hscal + 4 * r;
+  q.final_ctl = hc;
+  if (!q.done_ev) WS_CK(sv, cudaEventCreateWithFlags(&q.done_ev, cudaEventDisableTiming));
+  WS_CK(sv, cudaEventRecord(q.done_ev, c.stream));
+  q.state = 3;
+  pl.slot_req[r] = -1;
+  mark_free_kernel<<<1, 1, 0, c.stream>>>(pl.bb.ctl + r, 1);
+  WS_CK(sv, cudaGetLastError());
+  return WD_OK;
+}
+
+// a retired request whose download has completed: fill in its info
+wd_status finish(wd_server* sv, Request& q) {
+  const cudaError_t e = cudaEventQuery(q.done_ev);
+  if (e == cudaErrorNotReady) return WD_OK;
+  if (e != cudaSuccess) return serr(sv, WD_ERR_CUDA, std::string("request download: ") + cudaGetErrorString(e));
+  const double* h = sv->scal_pinned + 4 * q.scal_idx;
+  const SolverCtl& hc = q.final_ctl;
   const double b2 = h[0] + h[1], r2 = h[2] + h[3];
   wd_status rs = (wd_status)hc.status;
   if (rs == WD_OK && !hc.done) rs = WD_ERR_NOT_CONVERGED;
@@ -311,17 +415,27 @@ wd_status retire(wd_server* sv, Pool& pl, Request& q, int r, const SolverCtl& hc
   q.info.status = rs;
   q.info.kernel_launches = 0;
   q.state = 2;
-  pl.slot_req[r] = -1;
-  mark_free_kernel<<<1, 1, 0, c.stream>>>(pl.bb.ctl + r, 1);
-  WS_CK(sv, cudaGetLastError());
+  sv->scal_free.push_back(q.scal_idx);
+  q.scal_idx = -1;
+  cudaEventDestroy(q.done_ev);
+  q.done_ev = nullptr;
+  unpin(sv, q.b);
+  unpin(sv, q.x);
   return WD_OK;
 }
 
 // One pool: retire finished slots, release idle memory, admit, launch.
-wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory) {
+// did_work: a step completed, memory moved, a request was admitted or a step
+// launched (a pool that only waits for memory does nothing)
+wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& did_work) {
   const int prec = s->p.inner_precision;
   Ctx& c = pl.ctx->c;
+  did_work = false;
   if (pl.launched) {
+    did_work = true;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pl.start_ev, pl.done_ev) == cudaSuccess) s->st.gpu_step_seconds += 1e-3 * ms;
+    else cudaGetLastError();
     // retire the slots whose system finished during the step just completed
     WS_CK(s, cudaMemcpyAsync(pl.hctl, pl.bb.ctl, pl.capacity * sizeof(SolverCtl), cudaMemcpyDeviceToHost, c.stream));
     WS_CK(s, cudaStreamSynchronize(c.stream));
@@ -330,12 +444,14 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory) {
       wd_status st = retire(s, pl, s->reqs[pl.slot_req[r]], r, pl.hctl[r]);
       if (st != WD_OK) return st;
     }
-    WS_CK(s, cudaStreamSynchronize(c.stream));
     pl.launched = false;
   }
   bool busy = false;
   for (long long id : pl.slot_req) busy |= (id >= 0);
-  if (pl.capacity && !busy && pl.queue.empty()) release_workspace(pl, s->used);
+  if (pl.capacity && !busy && pl.queue.empty()) {
+    release_workspace(pl, s->used);
+    did_work = true;
+  }
   if (!pl.queue.empty() && !pl.capacity) {
     // slot memory: what the budget has left, shared with the other pools that wait
     const size_t left = s->p.budget_bytes ? (s->p.budget_bytes > s->used ? s->p.budget_bytes - s->used : 0)
@@ -348,6 +464,7 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory) {
       --waiting_for_memory;
       wd_status st = alloc_workspace(s, pl, cap);
       if (st != WD_OK) return st;
+      did_work = true;
     }
   }
   for (int r = 0; r < pl.capacity && !pl.queue.empty(); ++r) {
@@ -361,6 +478,9 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory) {
   for (long long id : pl.slot_req) n += (id >= 0);
   if (!n) return WD_OK;
   // up to iters_per_step lockstep iterations, then an event marks the end
+  if (!pl.start_ev) WS_CK(s, cudaEventCreate(&pl.start_ev));
+  if (!pl.done_ev) WS_CK(s, cudaEventCreate(&pl.done_ev));
+  WS_CK(s, cudaEventRecord(pl.start_ev, c.stream));
   batch_reset_kernel<<<1, 1, 0, c.stream>>>(pl.bb.bc, s->p.iters_per_step, s->p.use_graph ? 1 : 0, pl.hu, pl.hl);
   WS_CK(s, cudaGetLastError());
   if (s->p.use_graph) {
@@ -379,9 +499,10 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory) {
       if (hb.all_done) break;
     }
   }
-  if (!pl.done_ev) WS_CK(s, cudaEventCreateWithFlags(&pl.done_ev, cudaEventDisableTiming));
   WS_CK(s, cudaEventRecord(pl.done_ev, c.stream));
   pl.launched = true;
+  did_work = true;
+  ++s->st.steps;
   return WD_OK;
 }
 
@@ -406,10 +527,21 @@ wd_status wd_server_create(wd_server** out, const wd_server_params* p) {
 
 wd_status wd_server_destroy(wd_server* s) {
   if (!s) return WD_OK;
+  for (Pool& pl : s->pools)
+    if (pl.ctx) cudaStreamSynchronize(pl.ctx->c.stream);
+  for (auto& kv : s->reqs) {
+    if (kv.second.state == 3) finish(s, kv.second);
+    if (kv.second.done_ev) cudaEventDestroy(kv.second.done_ev);
+  }
+  for (auto& kv : s->pins)
+    if (kv.second.registered) cudaHostUnregister(const_cast<void*>(kv.first));
+  s->pins.clear();
+  if (s->scal_pinned) cudaFreeHost(s->scal_pinned);
   for (Pool& pl : s->pools) {
     if (pl.ctx) cudaStreamSynchronize(pl.ctx->c.stream);
     release_workspace(pl, s->used);
     if (pl.done_ev) cudaEventDestroy(pl.done_ev);
+    if (pl.start_ev) cudaEventDestroy(pl.start_ev);
     if (pl.ctx) {
       cudaStream_t st = pl.ctx->c.stream;
       wd_destroy(pl.ctx);
@@ -477,6 +609,9 @@ wd_status wd_server_submit(wd_server* s, int gauge_id, const double* b, double* 
         fixed + slot_bytes(pl.ctx->c, s->p.inner_precision) + small_bytes(pl.ctx->c, 1) > s->p.budget_bytes)
       return serr(s, WD_ERR_BUDGET, "one solver slot for this lattice exceeds the memory budget");
   }
+  const size_t field = (size_t)2 * s->pools[gauge_id].ctx->c.g.Vh * 24 * sizeof(double);
+  pin(s, b, field);
+  pin(s, x, field);
   Request q{};
   q.id = s->next_id++;
   q.pool = gauge_id;
@@ -513,16 +648,27 @@ wd_status wd_server_step(wd_server* s, int* active_out, int* queued_out) {
         for (long long id : pl.slot_req) busy |= (id >= 0);
         if (!busy && !pl.capacity) continue;
       }
-      wd_status st = pool_progress(s, pl, waiting);
+      bool did = false;
+      wd_status st = pool_progress(s, pl, waiting, did);
       if (st != WD_OK) return st;
-      progressed = true;
+      progressed |= did;
     }
     if (progressed || pass == 1) break;
-    for (Pool& pl : s->pools)
-      if (pl.launched) {
-        WS_CK(s, cudaEventSynchronize(pl.done_ev));
-        break;
+    // wait for whichever running pool finishes its step first
+    const auto tw = Clock::now();
+    for (;;) {
+      int running = 0;
+      bool ready = false;
+      for (Pool& pl : s->pools) {
+        if (!pl.launched) continue;
+        ++running;
+        if (cudaEventQuery(pl.done_ev) != cudaErrorNotReady) ready = true;
       }
+      if (!running || ready) break;
+      if (since(tw) > 600.0) return serr(s, WD_ERR_TIMEOUT, "no pool finished its step within 600 s");
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    s->st.wait_seconds += since(tw);
   }
   int active = 0, queued = 0;
   for (Pool& pl : s->pools) {
@@ -538,11 +684,21 @@ wd_status wd_server_poll(wd_server* s, long long request_id, int* finished, wd_s
   if (!s || !finished) return WD_ERR_INVALID_ARG;
   auto it = s->reqs.find(request_id);
   if (it == s->reqs.end()) return serr(s, WD_ERR_INVALID_ARG, "unknown request id");
+  if (it->second.state == 3) {
+    const wd_status st = finish(s, it->second);
+    if (st != WD_OK) return st;
+  }
   *finished = it->second.state == 2;
   if (*finished && info) *info = it->second.info;
   return WD_OK;
 }
 
 size_t wd_server_memory_in_use(const wd_server* s) { return s ? s->used : 0; }
+
+wd_status wd_server_get_stats(const wd_server* s, wd_server_stats* out) {
+  if (!s || !out) return WD_ERR_INVALID_ARG;
+  *out = s->st;
+  return WD_OK;
+}
 
 }  // extern "C"

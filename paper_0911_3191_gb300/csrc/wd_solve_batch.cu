@@ -469,15 +469,13 @@ wd_status wd_solve_batch(wd_ctx* ctx, int n, double* const* x, const double* con
   char* xf = bf + full * n;
   wd_status st = WD_OK;
   for (int r = 0; r < n && st == WD_OK; ++r) {
-    st = wd_field_import(ctx, bf + r * full, b[r], 0, WD_EVEN, WD_F64);
-    if (st == WD_OK) st = wd_field_import(ctx, bf + r * full + full / 2, b[r], 0, WD_ODD, WD_F64);
+    st = wd_internal_import_full(ctx, bf + r * full, bf + r * full + full / 2, b[r]);
   }
   wd_status rs = st;
   if (st == WD_OK) rs = solve_batch_device(ctx, n, xf, bf, kappas, params, infos);
   if (rs == WD_OK || rs == WD_ERR_NOT_CONVERGED || rs == WD_ERR_BREAKDOWN || rs == WD_ERR_NUMERIC) {
     for (int r = 0; r < n; ++r) {
-      wd_status s2 = wd_field_export(ctx, x[r], xf + r * full, 0, WD_EVEN, WD_F64);
-      if (s2 == WD_OK) s2 = wd_field_export(ctx, x[r], xf + r * full + full / 2, 0, WD_ODD, WD_F64);
+      wd_status s2 = wd_internal_export_full(ctx, x[r], xf + r * full, xf + r * full + full / 2);
       if (s2 != WD_OK) {
         rs = s2;
         break;
