@@ -77,7 +77,8 @@ FP64_PEAK_TFLOPS = 1.252
 # the dslash-only command of this file at 24^3x64); None where not captured
 # since the kernel last changed.
 # key: (precision, link reals, lattice, temporal gauge)
-NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", False): 650.13e6, ("q16", 12, "24x24x24x64", False): 112.31e6}
+NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", False): 650.13e6, ("f64", 18, "24x24x24x64", True): 525.69e6,
+                     ("q16", 12, "24x24x24x64", True): 90.70e6}
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
 
@@ -317,12 +318,17 @@ def run_ours(args):
 
     # ---- the same solve with every inner precision (one timed solve each)
     by_inner = {}
-    for name, prec in (("f32", wdp.F32), ("q16", wdp.Q16), ("h16n", wdp.H16N), ("b16n", wdp.B16N)):
-        solve(prec)
+    variants = [("f32", wdp.F32, False), ("q16", wdp.Q16, False), ("h16n", wdp.H16N, False),
+                ("b16n", wdp.B16N, False), ("q16_xhat_f32", wdp.Q16, True), ("b16n_xhat_f32", wdp.B16N, True)]
+    for name, prec, xf in variants:
+        def solve_v():
+            return wd.solve_device(fx, fb, kappa, tol=tol, delta=delta, solver=solver, inner_precision=prec,
+                                   use_graph=not args.host_loop, xhat_f32=xf)
+        solve_v()
         flush.add_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        ri = solve(prec)
+        ri = solve_v()
         e1.record(s)
         e1.synchronize()
         by_inner[name] = {"ms": round(e0.elapsed_time(e1), 3), "iters": ri.iters, "updates": ri.reliable_updates,

@@ -173,6 +173,10 @@ typedef struct {
                           relative to its starting residual, then x += p,
                           r = b - A x in FP64 and the Krylov iteration restarts
                           (not for batched solves; needs a lower inner precision) */
+  int xhat_f32;        /* 1: x_hat, the solution accumulated between reliable
+                          updates, is kept in FP32 when the inner precision is
+                          16-bit (Sec. 5.3 keeps it in the inner precision, the
+                          default 0); single solves only                        */
 } wd_solve_params;
 
 typedef struct {

@@ -8,6 +8,7 @@
 // conditions set on the device by the reduction finalisers -- or, with
 // use_graph = 0, as a host loop that reads the device control block each
 // iteration.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -455,8 +456,9 @@ wd_status ensure_solver(wd_ctx* ctx, int solver, int prec) {
     if (st != WD_OK) return st;
   }
   const size_t f64 = field_bytes(c, WD_F64), fin = field_bytes(c, prec);
+  const size_t fx = std::max(fin, field_bytes(c, WD_F32));  // x_hat may be FP32
   const int n_inner = (solver == WD_BICGSTAB) ? 7 : 5;
-  c.sb_bytes = 4 * f64 + n_inner * fin;
+  c.sb_bytes = 4 * f64 + (n_inner - 1) * fin + fx;
   wd_status st = dev_alloc(ctx, &c.sb_block, c.sb_bytes);
   if (st != WD_OK) return st;
   char* p = (char*)c.sb_block;
@@ -467,7 +469,7 @@ wd_status ensure_solver(wd_ctx* ctx, int solver, int prec) {
   c.sb.r_hat = p; p += fin;
   c.sb.p = p; p += fin;
   c.sb.v = p; p += fin;
-  c.sb.x_hat = p; p += fin;
+  c.sb.x_hat = p; p += fx;
   c.sb.tmp = p; p += fin;
   if (solver == WD_BICGSTAB) {
     c.sb.r_tilde = p; p += fin;
@@ -545,6 +547,7 @@ wd_status build_graph(wd_ctx* ctx, int solver, int prec, unsigned long long* h_u
   c.graph_exec = exec;
   c.graph_prec = prec;
   c.graph_solver = solver;
+  c.graph_xhat = c.sb.xhat_f32;
   *h_update = hu;
   *h_loop = hl;
   return WD_OK;
@@ -554,9 +557,10 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
                        wd_solve_info* info) {
   Ctx& c = ctx->c;
   const auto t0 = std::chrono::steady_clock::now();
-  wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_F64, 1, 0};
+  wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_F64, 1, 0, 0};
   if (prm) p = *prm;
   if (!valid_prec(p.inner_precision)) return set_err(ctx, WD_ERR_INVALID_ARG, "bad inner_precision");
+  if (p.xhat_f32 != 0 && p.xhat_f32 != 1) return set_err(ctx, WD_ERR_INVALID_ARG, "xhat_f32 must be 0 or 1");
   if (p.restart && p.inner_precision == WD_F64)
     return set_err(ctx, WD_ERR_INVALID_ARG, "defect correction needs a lower inner precision");
   if (p.solver != WD_BICGSTAB && p.solver != WD_CGNR) return set_err(ctx, WD_ERR_INVALID_ARG, "bad solver");
@@ -570,6 +574,7 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   const PrecOps* o64 = ops_f64();
   const PrecOps* oin = prec_ops(p.inner_precision);
   SolveBufs& sb = c.sb;
+  sb.xhat_f32 = p.xhat_f32;
   cudaStream_t s = c.stream;
   const size_t f64 = field_bytes(c, WD_F64);
   const char* b_e = (const char*)b_full;
@@ -587,7 +592,8 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
 
   unsigned long long hu = 0, hl = 0;
   if (p.use_graph) {
-    if (!(c.graph_exec && c.graph_prec == p.inner_precision && c.graph_solver == p.solver)) {
+    if (!(c.graph_exec && c.graph_prec == p.inner_precision && c.graph_solver == p.solver &&
+          c.graph_xhat == p.xhat_f32)) {
       destroy_graph(c);
       if ((st = build_graph(ctx, p.solver, p.inner_precision, &c.graph_hu, &c.graph_hl)) != WD_OK) return st;
     }

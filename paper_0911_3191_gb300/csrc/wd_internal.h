@@ -99,8 +99,9 @@ struct SolveBufs {
   void* p;              // inner
   void* v;              // inner: BiCGstab v, CG w
   void* t;              // inner: BiCGstab t
-  void* x_hat;          // inner: solution since the last reliable update
+  void* x_hat;          // inner (or FP32, xhat_f32): solution since the last reliable update
   void* tmp;            // inner odd temporary
+  int xhat_f32;         // x_hat kept in FP32 under a 16-bit inner precision
 };
 
 struct Ctx {
@@ -135,7 +136,7 @@ struct Ctx {
   void* sb_full[2];     // F64 full fields for host solves (b, x)
   cudaGraphExec_t graph_exec;
   cudaGraph_t graph;
-  int graph_prec, graph_solver;
+  int graph_prec, graph_solver, graph_xhat;
   unsigned long long graph_hu, graph_hl;  // conditional handles of the graph
   // batched solves (S11): workspace, graph and tuned launch shapes
   void* batch_block;

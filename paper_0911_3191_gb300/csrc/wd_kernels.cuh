@@ -348,10 +348,12 @@ struct EpiXpayNorm {
 
 // CG: q = w + c acc (= M_hat^dag M_hat p); x_hat += alpha p; r_hat -= alpha q;
 // reduce |r_hat|^2.  q is never stored.
-template <class S, class Fin>
+template <class S, class Fin, class SX = S>
 struct EpiCgUpdate {
   static constexpr int NRED = 1;
-  S w, p, xh, r;
+  S w, p;
+  SX xh;
+  S r;
   Coef c;
   const SolverCtl* ctl;
   RedScratch rs;
@@ -566,10 +568,11 @@ struct OpBicgS {
 };
 
 // x_hat += alpha p + omega s; r = s - omega t (s lives in r); reduce |r|^2, <r_tilde, r>
-template <class S>
+template <class S, class SX = S>
 struct OpBicgFinal {
   static constexpr int NRED = 3;
-  S xh, p, r, t, rt;
+  SX xh;
+  S p, r, t, rt;
   const SolverCtl* ctl;
   RedScratch rs;
   FinBicgIter fin;
@@ -980,13 +983,25 @@ struct Impl {
   }
 
   // ---- BiCGstab on M_hat (Sec. 5.1), inner precision P
+  // x_hat in FP32 instead of the 16-bit inner precision (SolveBufs::xhat_f32)
+  using TX = Tr<WD_F32>;
+  static bool xf32(const SolveBufs& b) { return b.xhat_f32 && T::S::kBytesPerSite < 96; }
+  static void zero_xhat(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    if (xf32(b)) launch_sites(c, c.g.Vh, OpZero<SpinorF32>{TX::view(b.x_hat, c.g)}, s);
+    else zero(c, b.x_hat, s);
+  }
+  static void accumulate(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+    if (xf32(b)) launch_sites(c, c.g.Vh, OpAccumulate<SpinorF32>{T64::view(b.x, c.g), TX::view(b.x_hat, c.g)}, s);
+    else launch_sites(c, c.g.Vh, OpAccumulate<S>{T64::view(b.x, c.g), T::view(b.x_hat, c.g)}, s);
+  }
+
   static void bicg_setup(const Ctx& c, SolveBufs& b, cudaStream_t s) {
     using Q = OpQuantDup<S, SpinorF64, FinBicgSetup>;
     launch_sites(c, c.g.Vh, Q{T::view(b.r_hat, c.g), T::view(b.r_tilde, c.g), T64::view(b.b_hat, c.g), c.red,
                                FinBicgSetup{b.ctl}}, s);
     zero(c, b.p, s);
     zero(c, b.v, s);
-    zero(c, b.x_hat, s);
+    zero_xhat(c, b, s);
   }
   static void bicg_iteration(const Ctx& c, SolveBufs& b, cudaStream_t s) {
     const Geom& g = c.g;
@@ -1009,16 +1024,23 @@ struct Impl {
       launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 0, e, s);
     }
     // x_hat += alpha p + omega s, r = s - omega t, |r|^2, rho = <r_tilde, r>
-    launch_sites(c, g.Vh,
-                 OpBicgFinal<S>{T::view(b.x_hat, g), T::view(b.p, g), T::view(b.r_hat, g), T::view(b.t, g),
-                                T::view(b.r_tilde, g), b.ctl, c.red, FinBicgIter{b.ctl}},
-                 s);
+    if (xf32(b))
+      launch_sites(c, g.Vh,
+                   OpBicgFinal<S, SpinorF32>{TX::view(b.x_hat, g), T::view(b.p, g), T::view(b.r_hat, g),
+                                             T::view(b.t, g), T::view(b.r_tilde, g), b.ctl, c.red,
+                                             FinBicgIter{b.ctl}},
+                   s);
+    else
+      launch_sites(c, g.Vh,
+                   OpBicgFinal<S>{T::view(b.x_hat, g), T::view(b.p, g), T::view(b.r_hat, g), T::view(b.t, g),
+                                  T::view(b.r_tilde, g), b.ctl, c.red, FinBicgIter{b.ctl}},
+                   s);
   }
   // Alg. 2 reliable update: x += x_hat, x_hat = 0, r = b_hat - M_hat x (FP64),
   // r_hat = r (quantised), rho = <r_tilde, r_hat>
   static void bicg_update(const Ctx& c, SolveBufs& b, cudaStream_t s) {
     const Geom& g = c.g;
-    launch_sites(c, g.Vh, OpAccumulate<S>{T64::view(b.x, g), T::view(b.x_hat, g)}, s);
+    accumulate(c, b, s);
     EpiStore<SpinorF64> e0{T64::view(b.tmp64, g)};
     launch_dslash<double>(c, T64::view(b.x, g), T64::gauge(c), 1, 0, e0, s);
     EpiRelupBicg<S, S, FinRelupBicg> e1{T64::view(b.b_hat, g), T64::view(b.x, g), T::view(b.r_hat, g),
@@ -1041,7 +1063,7 @@ struct Impl {
                                              FinCgSetup{b.ctl, c.scalars + 2}};
     launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 1, e1, s);
     zero(c, b.p, s);
-    zero(c, b.x_hat, s);
+    zero_xhat(c, b, s);
   }
   static void cg_iteration(const Ctx& c, SolveBufs& b, cudaStream_t s) {
     const Geom& g = c.g;
@@ -1055,7 +1077,11 @@ struct Impl {
     }
     // q = M_hat^dag w; x_hat += alpha p; r -= alpha q; |r|^2
     dslash(c, b.tmp, b.v, 1, 1, s);
-    {
+    if (xf32(b)) {
+      EpiCgUpdate<S, FinCgIter, SpinorF32> e{T::view(b.v, g), T::view(b.p, g), TX::view(b.x_hat, g),
+                                             T::view(b.r_hat, g), nk2, b.ctl, c.red, FinCgIter{b.ctl}};
+      launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 1, e, s);
+    } else {
       EpiCgUpdate<S, FinCgIter> e{T::view(b.v, g), T::view(b.p, g), T::view(b.x_hat, g), T::view(b.r_hat, g),
                                   nk2, b.ctl, c.red, FinCgIter{b.ctl}};
       launch_dslash<R>(c, T::view(b.tmp, g), T::gauge(c), 0, 1, e, s);
@@ -1064,7 +1090,7 @@ struct Impl {
   static void cg_update(const Ctx& c, SolveBufs& b, cudaStream_t s) {
     const Geom& g = c.g;
     const Coef nk2{0.0, &b.ctl->neg_kappa2};
-    launch_sites(c, g.Vh, OpAccumulate<S>{T64::view(b.x, g), T::view(b.x_hat, g)}, s);
+    accumulate(c, b, s);
     // r = b_hat - M_hat x  (FP64, stored)
     EpiStore<SpinorF64> e0{T64::view(b.tmp64, g)};
     launch_dslash<double>(c, T64::view(b.x, g), T64::gauge(c), 1, 0, e0, s);

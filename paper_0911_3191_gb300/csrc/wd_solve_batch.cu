@@ -222,7 +222,7 @@ wd_status solve_batch_device(wd_ctx* ctx, int n, void* x, const void* bsrc, cons
                              const wd_solve_params* prm, wd_solve_info* infos) {
   Ctx& c = ctx->c;
   const auto t0 = std::chrono::steady_clock::now();
-  wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_Q16, 1};
+  wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_Q16, 1, 0, 0};
   if (prm) p = *prm;
   if (n < 1 || n > kMaxBatch) return berr(ctx, WD_ERR_INVALID_ARG, "batch size must be in [1, 256]");
   if (p.inner_precision < WD_F64 || p.inner_precision > WD_B16N)

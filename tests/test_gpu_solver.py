@@ -175,3 +175,22 @@ def test_defect_correction_alg1(small, solver, prec, eps_in):
     assert r.reliable_updates >= 1
     with pytest.raises(m.WDError):
         wd.solve(x, b, kappa, inner_precision=0, restart=True)
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("prec", [2, 3, 4])
+def test_xhat_in_fp32(small, solver, prec):
+    """x_hat kept in FP32 under a 16-bit inner precision (the option of
+    keeping the accumulated correction above the inner precision): same
+    tolerance, same solution."""
+    m, wd, dims, kappa, U, b, x_ref, oracle_iters = small
+    x = np.zeros_like(b)
+    r = wd.solve(x, b, kappa, tol=1e-12, solver=solver, inner_precision=prec, xhat_f32=True)
+    rel = oracle.true_residual(x, b, U, dims, kappa)
+    assert r.status == 0 and rel <= 1e-12, (r, rel)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-9
+    # the graph and the host loop agree bit for bit with this option too
+    x2 = np.zeros_like(b)
+    r2 = wd.solve(x2, b, kappa, tol=1e-12, solver=solver, inner_precision=prec, xhat_f32=True, use_graph=False)
+    assert (r.iters, r.reliable_updates) == (r2.iters, r2.reliable_updates)
+    np.testing.assert_array_equal(x, x2)
