@@ -198,6 +198,16 @@ def cpu_baseline(U, b, dims, kappa, iters_full: int, sample_iters: int):
                       f"({dt:.1f} s), scaled to the {iters_full} iterations of the full FP64 solve"}
 
 
+def bench_config(args, ws):
+    """The workload both arms report (the reference arm runs it on the CPU oracle)."""
+    return {"workload": WORKLOAD["workload"], "lattice": "24x24x24x64", "solver": args.solver,
+            "fp64_link_reals": args.recon, "temporal_gauge": args.temporal_gauge,
+            "low_precision_links": "8 numbers" if args.recon8 else "12 reals",
+            "loop": "host" if args.host_loop else "cuda-graph",
+            "inner_precision": args.inner, "parallelism": f"replicas{ws}",
+            "l2": "flushed between timed solves (256 MB write); inputs (FP64 gauge 340 MB) exceed L2"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -216,7 +226,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W["workload"], "lattice": "24x24x24x64"},
+            "config": bench_config(args, ws),
             "cpu_baseline": {**vals[0], "value": v},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -382,12 +392,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1000 * t_total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.inner + "+f64", "data": "synthetic",
-            "config": {"workload": W["workload"], "lattice": "24x24x24x64", "solver": args.solver,
-                       "fp64_link_reals": args.recon, "temporal_gauge": args.temporal_gauge,
-                       "low_precision_links": "8 numbers" if args.recon8 else "12 reals",
-                       "loop": "host" if args.host_loop else "cuda-graph",
-                       "inner_precision": args.inner, "parallelism": f"replicas{ws}",
-                       "l2": "flushed between timed solves (256 MB write); inputs (FP64 gauge 340 MB) exceed L2"},
+            "config": bench_config(args, ws),
             "solve": {"iters": r0.iters, "reliable_updates": r0.reliable_updates,
                       "true_rel_residual": r0.true_rel_residual},
             "fp64_solve": {"ms_per_solve": round(1000 * f64_s, 3), "iters": f64_info.iters,

@@ -436,21 +436,21 @@ struct EpiRelupBicg {
     b.load(h, bv);
     x.load(h, xv);
     const double cc = c.get();
-    double n = 0.0;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) {
-      a[k] = bv[k] - (xv[k] + cc * a[k]);
-      n += a[k] * a[k];
-    }
-    red[0] += n;
-    // r_hat = r as stored in the inner precision; <r_tilde, r_hat> and
-    // |r_hat|^2 are inner-solver scalars: per-site partials in the inner
-    // precision's arithmetic (FP32 for FP32 and 16-bit storage), one FP64 add
-    // per site
+    for (int k = 0; k < 24; ++k) a[k] = bv[k] - (xv[k] + cc * a[k]);
+    // |r|^2 (the true-residual test of Alg. 2, needed to a few digits),
+    // <r_tilde, r_hat> and |r_hat|^2 (inner-solver scalars, r_hat = r as
+    // stored): per-site partials in the inner precision's arithmetic (FP32 for
+    // FP32 and 16-bit storage), one FP64 add per site each
     using RI = typename RH::real;
     RI q[24];
+    RI n = 0;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) q[k] = (RI)a[k];
+    for (int k = 0; k < 24; ++k) {
+      q[k] = (RI)a[k];
+      n += q[k] * q[k];
+    }
+    red[0] += (double)n;
     rh.store_get(h, q);
     RI wv[24];
     rt.load(h, wv);
