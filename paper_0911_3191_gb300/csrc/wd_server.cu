@@ -62,7 +62,6 @@ struct Pool {
   std::vector<long long> slot_req;  // -1 free
   std::deque<long long> queue;
   SolverCtl* hctl = nullptr;        // pinned mirror of the ctl array
-  double* hscal = nullptr;          // pinned mirror of per-slot scalars
   bool launched = false;            // a step of iterations is in flight
   cudaEvent_t start_ev = nullptr;   // recorded before the step's iterations
   cudaEvent_t done_ev = nullptr;    // recorded after them
@@ -141,9 +140,11 @@ int blas_gx_for(const Ctx& c, int n) {
   return std::max(1, std::min(per, need));
 }
 
-// launch shape for a capacity of n slots: right-hand sides per block no more
+// Launch shape for a capacity of n slots: right-hand sides per block no more
 // than the slots (a block's threads for absent systems idle), and enough
-// blocks that the sites of one system alone fill the device
+// blocks that the sites of one system alone fill the device.  (Choosing the
+// shape per step from the systems present, with one graph per shape, measured
+// no faster on the serving stream.)
 BatchLaunch pool_shape(const Ctx& c, int n) {
   const int ntiles = (c.g.Vh + 31) / 32;
   int tr = 1;
@@ -217,7 +218,6 @@ void release_workspace(Pool& pl, size_t& used) {
   if (pl.hctl) cudaFreeHost(pl.hctl);
   pl.ws = pl.small = nullptr;
   pl.hctl = nullptr;
-  pl.hscal = nullptr;
   used -= pl.ws_bytes;
   pl.ws_bytes = 0;
   pl.capacity = 0;
@@ -238,9 +238,11 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
     pl.ws = nullptr;
     return serr(sv, WD_ERR_OOM, "slot control allocation failed");
   }
-  WS_CK(sv, cudaMemset(pl.small, 0, sm));
-  WS_CK(sv, cudaMallocHost((void**)&pl.hctl, (size_t)cap * sizeof(SolverCtl) + 4 * (size_t)cap * 8 + 64));
-  pl.hscal = (double*)((char*)pl.hctl + (size_t)cap * sizeof(SolverCtl));
+  // on the pool's stream: a plain cudaMemset runs on the legacy default
+  // stream, which is not ordered with the pool's non-blocking stream and could
+  // land after the slots' control blocks are initialised
+  WS_CK(sv, cudaMemsetAsync(pl.small, 0, sm, c.stream));
+  WS_CK(sv, cudaMallocHost((void**)&pl.hctl, (size_t)cap * sizeof(SolverCtl)));
   pl.ws_bytes = ws + sm;
   sv->used += pl.ws_bytes;
   pl.capacity = cap;
@@ -449,6 +451,8 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& d
   bool busy = false;
   for (long long id : pl.slot_req) busy |= (id >= 0);
   if (pl.capacity && !busy && pl.queue.empty()) {
+    // the retirements just enqueued still read the slot fields
+    WS_CK(s, cudaStreamSynchronize(c.stream));
     release_workspace(pl, s->used);
     did_work = true;
   }

@@ -114,7 +114,7 @@ wd_status ensure_batch(wd_ctx* ctx, int n, int prec) {
   }
   const SmallLayout L = small_layout(c, n);
   e = cudaMalloc(&c.batch_small, L.total);
-  if (e == cudaSuccess) e = cudaMemset(c.batch_small, 0, L.total);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.batch_small, 0, L.total, c.stream);  // ordered with the solve
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c.batch_host, (size_t)n * sizeof(SolverCtl) + 4 * n * 8 + 64);
   if (e != cudaSuccess) {
     cudaGetLastError();

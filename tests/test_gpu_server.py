@@ -109,3 +109,27 @@ def test_budget_too_small_is_refused(fields):
         srv.add_gauge(dims, fields[dims])
     assert e.value.status == 8  # WD_ERR_BUDGET
     srv.close()
+
+
+def test_pool_release_and_reallocation(fields):
+    """A pool that drains releases its slot memory and allocates it again for
+    the next request, while another pool keeps the device busy: every result
+    still matches the oracle (the re-allocated control blocks are initialised
+    in stream order)."""
+    import paper_0911_3191_gb300 as m
+    big, small = (8, 8, 8, 16), (4, 6, 8, 10)
+    srv = m.Server(max_slots=2, iters_per_step=3, inner_precision=m.Q16)
+    g_big, g_small = srv.add_gauge(big, fields[big]), srv.add_gauge(small, fields[small])
+    busy = [srv.submit(g_big, li.gaussian_spinor(big, 2600 + k), 0.124, 1e-12) for k in range(6)]
+    checks = []
+    for k in range(8):
+        b = li.gaussian_spinor(small, 2700 + k)
+        rid = srv.submit(g_small, b, 0.12, 1e-10)
+        res = _drain(srv, [rid])[rid]
+        checks.append((b, res))
+    _drain(srv, list(busy))
+    for b, (res, x) in checks:
+        rel = oracle.true_residual(x, b, fields[small], small, 0.12)
+        assert res.status == 0 and rel <= 1e-10 and res.iters > 2, (res, rel)
+    assert srv.stats()["retired"] == 14
+    srv.close()
