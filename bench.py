@@ -732,7 +732,7 @@ def run_serve(args):
     tols = np.array([1e-8, 1e-10, 1e-12])[rng.integers(0, 3, size=n)]
     inner = wdp.PREC_BY_NAME[args.inner]
     srv = wdp.Server(budget_bytes=80 * 1000**3, max_slots=args.serve_slots, iters_per_step=args.serve_iters,
-                     inner_precision=inner, delta=0.1, temporal_gauge=args.temporal_gauge)
+                     inner_precision=inner, delta=0.1, temporal_gauge=args.temporal_gauge, rhs_tile=args.serve_tile)
     gids, srcs, outs = {}, {}, {}
     t0 = time.perf_counter()
     for v, dims in enumerate(vols):
@@ -808,6 +808,7 @@ def run_serve(args):
                       "latency_p50_s": round(float(np.percentile(lat_a, 50)), 3),
                       "latency_p99_s": round(float(np.percentile(lat_a, 99)), 3), "per_volume": per_vol,
                       "setup_s": round(setup_s, 1), "max_slots": args.serve_slots, "iters_per_step": args.serve_iters,
+                      "rhs_tile": args.serve_tile,
                       "one_at_a_time_s": round(serial, 2), "efficiency_vs_one_at_a_time": round(serial / makespan, 3),
                       "server_stats": server_stats, "host_step_s": round(t_step, 2), "host_poll_s": round(t_poll, 2),
                       "failures": failures[:10],
@@ -849,6 +850,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-iters", type=int, default=8)
+    ap.add_argument("--serve-tile", type=int, default=0, choices=[-1, 0, 1, 2, 4],
+                    help="systems per link tile of the inner dslash (-1 one per block row, 0 automatic)")
     ap.add_argument("--serve-volumes", default="0,1,2,3",
                     help="which of the four volumes (16^3x32, 24^3x48, 32^3x64, 48^3x96) requests go to")
     args = ap.parse_args()

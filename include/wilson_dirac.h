@@ -256,6 +256,9 @@ typedef struct {
   int max_iter;        /* per request                                                 */
   int use_graph;       /* 1: each step's iterations run as one CUDA graph             */
   int gauge_flags;     /* wd_gauge_flags for every gauge field (wd_load_gauge_opt)    */
+  int rhs_tile;        /* inner multi-RHS dslash: systems sharing a link tile (1, 2 or
+                          4), -1 one system per block row, 0 chosen from the pool's
+                          capacity                                                    */
 } wd_server_params;
 
 wd_status wd_server_create(wd_server **out, const wd_server_params *params);

@@ -60,7 +60,7 @@ class ServerStats(ctypes.Structure):
 class ServerParams(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("iters_per_step", ctypes.c_int),
                 ("inner_precision", ctypes.c_int), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("gauge_flags", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("gauge_flags", ctypes.c_int), ("rhs_tile", ctypes.c_int)]
 
 
 _lib = None
@@ -349,13 +349,13 @@ class Server:
     fields, a device-memory budget, requests admitted as slots free up."""
 
     def __init__(self, budget_bytes=0, max_slots=8, iters_per_step=8, inner_precision=Q16, delta=0.1,
-                 max_iter=20000, use_graph=True, temporal_gauge=False, recon8=False):
+                 max_iter=20000, use_graph=True, temporal_gauge=False, recon8=False, rhs_tile=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the Wilson-Dirac library runs on the GPU only")
         self.lib = load_library()
         p = ServerParams(int(budget_bytes), int(max_slots), int(iters_per_step), int(inner_precision), float(delta),
-                         int(max_iter), int(use_graph), gauge_flags(temporal_gauge, recon8))
+                         int(max_iter), int(use_graph), gauge_flags(temporal_gauge, recon8), int(rhs_tile))
         h = ctypes.c_void_p()
         st = self.lib.wd_server_create(ctypes.byref(h), ctypes.byref(p))
         if st != 0:

@@ -215,6 +215,44 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
   }
 }
 
+// Per-system dslash over a batch: the single-system site kernel with
+// blockIdx.y naming the system (in mode 1, the y-th entry of the list of
+// systems due for an update; blocks past the list's end return at once).
+// Always used for FP64, where the FP64 pipe, not the link bytes, sets the
+// time, so sharing a link tile between systems gains nothing, while a tile
+// whose systems are mostly idle (one reliable update due among several)
+// leaves the SM a few computing warps; used for the inner precision when the
+// launch shape says so (tr = 0: few systems).
+template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G, class Epi>
+__global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRED, TFIX, R8>::kMinBlocks))
+    dslash_rhs_kernel(Geom g, In in, G gauge, int parity, Epi epi, BatchArgs ba) {
+  constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
+  const int i = blockIdx.y;
+  int r = i;
+  if (ba.mode == 1 && ba.bc) {
+    const int nwork = *(const volatile int*)&ba.bc->nupd;
+    r = i < nwork ? ba.bc->upd_list[i] : ba.nrhs;
+  }
+  if (!rhs_active(ba, r)) return;  // uniform over the block
+  const In v = in.at(r);
+  const Epi e = epi.at(r);
+  double red[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) red[k] = 0.0;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+    R acc[24];
+    dslash_site<DAGGER, TFIX, R8>(g, v, gauge, h, parity, acc);
+    e(h, acc, red);
+  }
+  if constexpr (Epi::NRED > 0) {
+    __shared__ double sm[32][NR];
+    block_sum<NR>(red, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NR; ++k) ba.partials[((size_t)r * NR + k) * gridDim.x + blockIdx.x] = red[k];
+  }
+}
+
 // Site kernel over a batch: blockIdx.y is the right-hand side.
 template <class Op>
 __global__ void __launch_bounds__(kBlasBlock) site_batch_kernel(int n, Op op, BatchArgs ba) {
@@ -286,12 +324,18 @@ __global__ void batch_init_kernel(SolverCtl* ctl, BatchCtl* bc, int nrhs, double
 // ------------------------------------------------------------ launchers
 struct BatchLaunch {
   int nrhs;
-  int tr;       // right-hand sides per chunk (1, 2, 4 or 8), inner precision
-  int grid;     // multi-RHS dslash blocks, inner precision
+  int tr;       // right-hand sides per chunk (1, 2, 4 or 8), inner precision;
+                // 0: one system per block row (dslash_rhs_kernel)
+  int grid;     // multi-RHS dslash blocks (tr = 0: blocks per system), inner precision
   int blas_gx;  // site-kernel blocks per right-hand side
-  int tr64 = 8;      // the FP64 (reliable-update) dslash: bound by the FP64 pipe,
-  int grid64 = 0;    // it wants many warps; 0 = same grid as the inner precision
+  int grid64 = 0;    // FP64 dslash (dslash_rhs_kernel): blocks per system; 0 = grid
 };
+
+// blocks per system of the FP64 per-system dslash: the single-system grid
+inline int rhs_grid64(const Geom& g, int num_sms) {
+  const int b = (g.Vh + kDslashBlock - 1) / kDslashBlock;
+  return b < num_sms * 16 ? b : num_sms * 16;
+}
 
 template <typename R>
 inline int mrhs_grid(const BatchLaunch& bl) {
@@ -303,8 +347,27 @@ void launch_dslash_mrhs(const Geom& g, const BatchLaunch& bl, const In& in, cons
                         const Epi& epi, const BatchArgs& ba, cudaStream_t s) {
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   const size_t smem = tile_link_bytes<R>() + (size_t)bl.nrhs * NR * sizeof(double);
-  const int tr = (sizeof(R) == 8) ? bl.tr64 : bl.tr;
   const int grid = mrhs_grid<R>(bl);
+  if (sizeof(R) == 8 || bl.tr == 0) {
+    const dim3 gr(grid, bl.nrhs);
+    auto go = [&](auto dag, auto tfix, auto rec8) {
+      dslash_rhs_kernel<decltype(dag)::value, decltype(tfix)::value, decltype(rec8)::value, R, In, G, Epi>
+          <<<gr, kDslashBlock, 0, s>>>(g, in, gauge, parity, epi, ba);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if constexpr (sizeof(R) == 4) {
+      if (gauge.recon == 8) {
+        if (g.tfix) dagger ? go(T_{}, T_{}, T_{}) : go(F_{}, T_{}, T_{});
+        else dagger ? go(T_{}, F_{}, T_{}) : go(F_{}, F_{}, T_{});
+        return;
+      }
+    }
+    if (g.tfix) dagger ? go(T_{}, T_{}, F_{}) : go(F_{}, T_{}, F_{});
+    else dagger ? go(T_{}, F_{}, F_{}) : go(F_{}, F_{}, F_{});
+    return;
+  }
+  const int tr = bl.tr;
 #define WD_MRHS_CASE(TRV)                                                                                   \
   case TRV:                                                                                                 \
     if (dagger)                                                                                             \
@@ -391,12 +454,12 @@ struct ImplBatch {
     launch_dslash_mrhs<R>(g, bl, v(b.p, g), T::gauge(c), 1, 0, e0, ba, s);
     EpiXpayDot<S, S, S, FinBicgAlpha> e1{v(b.v, g), v(b.p, g), v(b.r_tilde, g), nk2, c.red, FinBicgAlpha{b.ctl}};
     launch_dslash_mrhs<R>(g, bl, v(b.tmp, g), T::gauge(c), 0, 0, e1, ba, s);
-    launch_finalize<2>(bl, ba, bl.grid, FinBicgAlpha{b.ctl}, b.bc, 0, 0, s);
+    launch_finalize<2>(bl, ba, mrhs_grid<R>(bl), FinBicgAlpha{b.ctl}, b.bc, 0, 0, s);
     launch_sites_batch(g, bl, OpBicgS<S>{v(b.r_hat, g), v(b.v, g), b.ctl}, ba, s);
     launch_dslash_mrhs<R>(g, bl, v(b.r_hat, g), T::gauge(c), 1, 0, e0, ba, s);
     EpiXpayTS<S, S, FinBicgOmega> e2{v(b.t, g), v(b.r_hat, g), nk2, c.red, FinBicgOmega{b.ctl}};
     launch_dslash_mrhs<R>(g, bl, v(b.tmp, g), T::gauge(c), 0, 0, e2, ba, s);
-    launch_finalize<3>(bl, ba, bl.grid, FinBicgOmega{b.ctl}, b.bc, 1, 0, s);
+    launch_finalize<3>(bl, ba, mrhs_grid<R>(bl), FinBicgOmega{b.ctl}, b.bc, 1, 0, s);
     OpBicgFinal<S> fo{v(b.x_hat, g), v(b.p, g), v(b.r_hat, g), v(b.t, g), v(b.r_tilde, g), b.ctl, c.red,
                       FinBicgIter{b.ctl}};
     launch_sites_batch(g, bl, fo, ba, s);

@@ -98,6 +98,7 @@ constexpr float kInv32767 = 3.0518509475997192e-05f;  // (float)(1.0 / 32767.0)
 struct SpinorF64 {
   using real = double;
   static constexpr bool kScaled = false;
+  static constexpr float kBias = 0.f;
   double2* p;
   int stride;
   size_t rs;  // bytes from one right-hand side's field to the next (batches)
@@ -142,6 +143,7 @@ struct SpinorF64 {
 struct SpinorF32 {
   using real = float;
   static constexpr bool kScaled = false;
+  static constexpr float kBias = 0.f;
   float4* p;
   int stride;
   size_t rs;
@@ -249,6 +251,34 @@ struct Spinor16 {
     } else {
       return make_float2(lo(w), hi(w));
     }
+  }
+  // Q16 codes decoded without the final subtraction carry this offset
+  static constexpr float kBias = (F == Fmt16::Q16) ? 8421376.0f : 0.0f;
+  static __device__ __forceinline__ float2 pair_biased(uint32_t w) {
+    if constexpr (F == Fmt16::Q16) {
+      const uint32_t x = w ^ 0x80008000u;
+      return make_float2(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)),
+                         __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)));
+    } else {
+      return pair(w);
+    }
+  }
+  // load_raw() with Q16 codes left as q + kBias (see project_biased)
+  __device__ __forceinline__ float load_raw_biased(int h, float (&v)[24]) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint4 d = __ldg(p + (size_t)c * stride + h);
+      const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = pair_biased(w[j]);
+        v[8 * c + 2 * j] = f.x;
+        v[8 * c + 2 * j + 1] = f.y;
+      }
+    }
+    float n = __ldg(norm + h);
+    if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
+    else return n;
   }
   // raw 16-bit values as float (codes, or the normalised fp16/bf16 numbers)
   // plus the factor that turns them into field values
@@ -654,6 +684,43 @@ __device__ __forceinline__ void project(const R (&p)[24], R (&h)[12]) {
   }
 }
 
+// project() on values that all carry the offset B (Q16 codes decoded as
+// q + B, B = 2^23 + 2^15): a difference cancels B exactly; a sum is formed as
+// (a - 2B) + b, exact because both terms and the result are integers below
+// 2^24.  The results equal project() on the codes q, bit for bit, with one
+// add per projected value instead of three.
+template <int SG>
+__device__ __forceinline__ float pm_biased(float a, float b, float twoB) {
+  if constexpr (SG > 0) return __fadd_rn(__fsub_rn(a, twoB), b);
+  else return __fsub_rn(a, b);
+}
+template <int MU, int S_>
+__device__ __forceinline__ void project_biased(const float (&p)[24], float (&h)[12], float B) {
+  static_assert(MU < 3, "temporal hops are diagonal in this basis");
+  constexpr int S = (MU == 1) ? -S_ : S_;
+  const float twoB = 2.0f * B;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float p0r = p[(0 + c) * 2], p0i = p[(0 + c) * 2 + 1];
+    const float p1r = p[(3 + c) * 2], p1i = p[(3 + c) * 2 + 1];
+    const float p2r = p[(6 + c) * 2], p2i = p[(6 + c) * 2 + 1];
+    const float p3r = p[(9 + c) * 2], p3i = p[(9 + c) * 2 + 1];
+    float h0r, h0i, h1r, h1i;
+    if constexpr (MU == 0) {
+      h0r = pm_biased<-S>(p0r, p3i, twoB); h0i = pm_biased<S>(p0i, p3r, twoB);
+      h1r = pm_biased<-S>(p1r, p2i, twoB); h1i = pm_biased<S>(p1i, p2r, twoB);
+    } else if constexpr (MU == 1) {
+      h0r = pm_biased<-S>(p0r, p3r, twoB); h0i = pm_biased<-S>(p0i, p3i, twoB);
+      h1r = pm_biased<S>(p1r, p2r, twoB); h1i = pm_biased<S>(p1i, p2i, twoB);
+    } else {
+      h0r = pm_biased<-S>(p0r, p2i, twoB); h0i = pm_biased<S>(p0i, p2r, twoB);
+      h1r = pm_biased<S>(p1r, p3i, twoB); h1i = pm_biased<-S>(p1i, p3r, twoB);
+    }
+    h[c * 2] = h0r; h[c * 2 + 1] = h0i;
+    h[(3 + c) * 2] = h1r; h[(3 + c) * 2 + 1] = h1i;
+  }
+}
+
 template <int MU, int S_, typename R>
 __device__ __forceinline__ void reconstruct(const R (&g)[12], R (&a)[24]) {
   static_assert(MU < 3, "temporal hops are diagonal in this basis");
@@ -785,10 +852,15 @@ __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, in
   constexpr bool kScaled = In::kScaled || G::kScaled;
   R psi[24];
   R w = 1;
-  if constexpr (In::kScaled) w = in.load_raw(h_nbr, psi);
-  else in.load(h_nbr, psi);
   R hs[12];
-  project<MU, S>(psi, hs);
+  if constexpr (In::kScaled && In::kBias != 0.f) {
+    w = in.load_raw_biased(h_nbr, psi);
+    project_biased<MU, S>(psi, hs, In::kBias);
+  } else {
+    if constexpr (In::kScaled) w = in.load_raw(h_nbr, psi);
+    else in.load(h_nbr, psi);
+    project<MU, S>(psi, hs);
+  }
   R u[18];
   gauge.template load_scaled<R8>(FWD ? parity : 1 - parity, MU, h_link, u, w);
   R gs[12];

@@ -146,7 +146,8 @@ struct Ctx {
   cudaGraphExec_t batch_exec;
   cudaGraph_t batch_graph;
   unsigned long long batch_hu, batch_hl;
-  int batch_tr, batch_grid;  // tuned multi-RHS dslash shape for (batch_n, batch_prec)
+  int batch_tr, batch_grid;  // tuned multi-RHS dslash shape for (batch_n, batch_prec);
+                             // batch_tr 0: not tuned, -1: one system per block row
   double* batch_host;     // pinned mirror of per-system results
   std::string last_error;
 };

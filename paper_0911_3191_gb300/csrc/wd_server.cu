@@ -140,25 +140,30 @@ int blas_gx_for(const Ctx& c, int n) {
   return std::max(1, std::min(per, need));
 }
 
-// Launch shape for a capacity of n slots: right-hand sides per block no more
-// than the slots (a block's threads for absent systems idle), and enough
-// blocks that the sites of one system alone fill the device.  (Choosing the
-// shape per step from the systems present, with one graph per shape, measured
-// no faster on the serving stream.)
-BatchLaunch pool_shape(const Ctx& c, int n) {
+// Launch shape for a capacity of n slots.  rhs_tile > 0 (or 0 with more than
+// two slots): right-hand sides per block no more than the slots (a block's
+// threads for absent systems idle), and enough blocks that the sites of one
+// system alone fill the device.  rhs_tile -1 (or 0 with one or two slots):
+// one system per block row, the single-system grid, blocks of absent systems
+// return at once.  (Choosing the shape per step from the systems present,
+// with one graph per shape, measured no faster on the serving stream.)
+BatchLaunch pool_shape(const Ctx& c, int n, int rhs_tile) {
   const int ntiles = (c.g.Vh + 31) / 32;
   int tr = 1;
-  while (tr < n && tr < 4) tr *= 2;
-  int tr64 = 1;
-  while (tr64 < n && tr64 < 8) tr64 *= 2;
-  BatchLaunch bl{n, tr, std::min(c.num_sms * (64 / tr), ntiles), blas_gx_for(c, n)};
-  bl.tr64 = tr64;
-  bl.grid64 = std::min(c.num_sms * (32 / tr64), ntiles);
+  if (rhs_tile > 0) {
+    tr = rhs_tile;
+  } else {
+    while (tr < n && tr < 4) tr *= 2;
+    if (rhs_tile < 0 || n <= 2) tr = 0;
+  }
+  BatchLaunch bl{n, tr, tr ? std::min(c.num_sms * (64 / tr), ntiles) : rhs_grid64(c.g, c.num_sms),
+                 blas_gx_for(c, n)};
+  bl.grid64 = rhs_grid64(c.g, c.num_sms);
   return bl;
 }
 
-size_t small_bytes(const Ctx& c, int n) {
-  const BatchLaunch bl = pool_shape(c, n);
+size_t small_bytes(const Ctx& c, int n, int rhs_tile) {
+  const BatchLaunch bl = pool_shape(c, n, rhs_tile);
   const int maxblk = std::max(std::max(bl.grid, bl.grid64), bl.blas_gx);
   return align256((size_t)n * sizeof(SolverCtl)) + align256(sizeof(BatchCtl)) +
          align256((size_t)maxblk * n * 4 * sizeof(double)) + align256((size_t)2 * n * 8) + align256((size_t)4 * n * 8);
@@ -230,7 +235,7 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
   Ctx& c = pl.ctx->c;
   const int prec = sv->p.inner_precision;
   const size_t f64 = fbytes(c, WD_F64), fin = fbytes(c, prec);
-  const size_t ws = slot_bytes(c, prec) * cap, sm = small_bytes(c, cap);
+  const size_t ws = slot_bytes(c, prec) * cap, sm = small_bytes(c, cap, sv->p.rhs_tile);
   WS_CK(sv, cudaMalloc(&pl.ws, ws));
   if (cudaMalloc(&pl.small, sm) != cudaSuccess) {
     cudaGetLastError();
@@ -256,7 +261,7 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
   s += align256(sizeof(BatchCtl));
   b.partials = (double*)s;
   {
-    const BatchLaunch bl = pool_shape(c, cap);
+    const BatchLaunch bl = pool_shape(c, cap, sv->p.rhs_tile);
     s += align256((size_t)std::max(std::max(bl.grid, bl.grid64), bl.blas_gx) * cap * 4 * sizeof(double));
   }
   b.kappas = (double*)s;
@@ -274,7 +279,7 @@ wd_status alloc_workspace(wd_server* sv, Pool& pl, int cap) {
   b.t = p; p += fin * cap;
   b.x_hat = p; p += fin * cap;
   b.tmp = p; p += fin * cap;
-  pl.bl = pool_shape(c, cap);
+  pl.bl = pool_shape(c, cap, sv->p.rhs_tile);
   mark_free_kernel<<<(cap + 127) / 128, 128, 0, c.stream>>>(b.ctl, cap);
   WS_CK(sv, cudaGetLastError());
   if (sv->p.use_graph) {
@@ -462,8 +467,9 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& d
                                           : (size_t)-1;
     const size_t share = s->p.budget_bytes ? left / (size_t)std::max(1, waiting_for_memory) : left;
     int cap = s->p.max_slots;
-    while (cap > 0 && s->p.budget_bytes && slot_bytes(c, prec) * cap + small_bytes(c, cap) > share) --cap;
-    if (cap < 1 && s->p.budget_bytes && slot_bytes(c, prec) + small_bytes(c, 1) <= left) cap = 1;
+    while (cap > 0 && s->p.budget_bytes && slot_bytes(c, prec) * cap + small_bytes(c, cap, s->p.rhs_tile) > share)
+      --cap;
+    if (cap < 1 && s->p.budget_bytes && slot_bytes(c, prec) + small_bytes(c, 1, s->p.rhs_tile) <= left) cap = 1;
     if (cap >= 1) {
       --waiting_for_memory;
       wd_status st = alloc_workspace(s, pl, cap);
@@ -522,6 +528,7 @@ wd_status wd_server_create(wd_server** out, const wd_server_params* p) {
     return WD_ERR_INVALID_ARG;
   if (p->inner_precision != WD_F64 && !(p->delta > 0.0 && p->delta < 1.0)) return WD_ERR_INVALID_ARG;
   if (p->gauge_flags & ~(WD_GAUGE_TEMPORAL | WD_GAUGE_RECON8)) return WD_ERR_INVALID_ARG;
+  if (!(p->rhs_tile >= -1 && p->rhs_tile <= 2) && p->rhs_tile != 4) return WD_ERR_INVALID_ARG;
   wd_server* s = new (std::nothrow) wd_server();
   if (!s) return WD_ERR_OOM;
   s->p = *p;
@@ -610,7 +617,8 @@ wd_status wd_server_submit(wd_server* s, int gauge_id, const double* b, double* 
     size_t fixed = 0;
     for (const Pool& q : s->pools) fixed += q.fixed_bytes;
     if (s->p.budget_bytes &&
-        fixed + slot_bytes(pl.ctx->c, s->p.inner_precision) + small_bytes(pl.ctx->c, 1) > s->p.budget_bytes)
+        fixed + slot_bytes(pl.ctx->c, s->p.inner_precision) + small_bytes(pl.ctx->c, 1, s->p.rhs_tile) >
+            s->p.budget_bytes)
       return serr(s, WD_ERR_BUDGET, "one solver slot for this lattice exceeds the memory budget");
   }
   const size_t field = (size_t)2 * s->pools[gauge_id].ctx->c.g.Vh * 24 * sizeof(double);

@@ -11,6 +11,7 @@
 // tile, grid) is chosen by timing candidates on first use (autotuner), cached
 // per (lattice, precision, n) in the context and optionally in the file named
 // by the WD_TUNE_CACHE environment variable.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -149,8 +150,8 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
       if (bar != std::string::npos && line.substr(0, bar) == key) {
         std::istringstream v(line.substr(bar + 1));
         int tr = 0, grid = 0;
-        if (v >> tr >> grid && (tr == 1 || tr == 2 || tr == 4 || tr == 8) && grid > 0) {
-          c.batch_tr = tr;
+        if (v >> tr >> grid && (tr == 0 || tr == 1 || tr == 2 || tr == 4 || tr == 8) && grid > 0) {
+          c.batch_tr = tr ? tr : -1;
           c.batch_grid = grid;
           return WD_OK;
         }
@@ -167,12 +168,15 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
   WB_CK(ctx, cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tr = 4, best_grid = c.num_sms * 4;
-  const int trs[4] = {1, 2, 4, 8};
+  // tr 0: one system per block row, 128 sites per block
+  const int trs[5] = {0, 1, 2, 4, 8};
   const int mults[4] = {2, 4, 8, 16};
-  for (int ti = 0; ti < 4; ++ti) {
+  const int nblk128 = (c.g.Vh + kDslashBlock - 1) / kDslashBlock;
+  for (int ti = 0; ti < 5; ++ti) {
     for (int mi = 0; mi < 4; ++mi) {
       int grid = c.num_sms * mults[mi];
-      if (grid > ntiles) grid = ntiles;
+      const int cap = trs[ti] ? ntiles : nblk128;
+      if (grid > cap) grid = cap;
       bl.tr = trs[ti];
       bl.grid = grid;
       o->dslash_batch(c, bl, b.tmp, b.r_hat, 1, 0, c.stream);  // warm-up
@@ -192,7 +196,7 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   WB_CK_LAUNCH(ctx);
-  c.batch_tr = best_tr;
+  c.batch_tr = best_tr ? best_tr : -1;
   c.batch_grid = best_grid;
   if (cache) {
     std::ofstream f(cache, std::ios::app);
@@ -203,10 +207,10 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
 
 BatchLaunch launch_shape(const Ctx& c, int n) {
   const int ntiles = (c.g.Vh + 31) / 32;
-  BatchLaunch bl{n, c.batch_tr ? c.batch_tr : 4, c.batch_tr ? c.batch_grid : c.num_sms * 4, blas_gx(c, n)};
-  if (bl.grid > ntiles) bl.grid = ntiles;
-  bl.tr64 = 8;
-  bl.grid64 = c.num_sms * 4 < ntiles ? c.num_sms * 4 : ntiles;
+  BatchLaunch bl{n, c.batch_tr ? std::max(c.batch_tr, 0) : 4, c.batch_tr ? c.batch_grid : c.num_sms * 4,
+                 blas_gx(c, n)};
+  if (bl.tr && bl.grid > ntiles) bl.grid = ntiles;
+  bl.grid64 = rhs_grid64(c.g, c.num_sms);
   return bl;
 }
 
@@ -433,11 +437,11 @@ wd_status wd_dslash_batch(wd_ctx* ctx, void* out, const void* in, int nrhs, wd_p
   if (st != WD_OK) return st;
   BatchLaunch bl{nrhs, 4, c.num_sms * 4, blas_gx(c, nrhs)};
   if (c.batch_tr && c.batch_n == nrhs && c.batch_prec == prec) {
-    bl.tr = c.batch_tr;
+    bl.tr = std::max(c.batch_tr, 0);
     bl.grid = c.batch_grid;
   }
   const int ntiles = (c.g.Vh + 31) / 32;
-  if (bl.grid > ntiles) bl.grid = ntiles;
+  if (bl.tr && bl.grid > ntiles) bl.grid = ntiles;
   prec_ops(prec)->dslash_batch(c, bl, out, in, out_parity, dagger ? 1 : 0, c.stream);
   WB_CK_LAUNCH(ctx);
   return WD_OK;

@@ -125,3 +125,39 @@ def test_batch_with_zero_source(batch_problem):
     assert all(i.status == 0 for i in infos)
     assert np.all(xs[1] == 0)
     assert oracle.true_residual(xs[2], b2[2], U, dims, 0.12) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 2, 4])
+def test_per_system_shape(tmp_path, monkeypatch, prec):
+    """The batched dslash and solver with the inner dslash forced to one system
+    per block row (a tuning-cache entry with tile 0) agree with the oracle."""
+    import paper_0911_3191_gb300 as m
+    dims = (8, 6, 4, 16)
+    U = li.gauge(dims, 0.5, 1012)
+    nrhs = 3
+    cache = tmp_path / "tune.txt"
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cache.write_text(f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} prec{prec} n{nrhs} sms{sms}|0 8\n")
+    monkeypatch.setenv("WD_TUNE_CACHE", str(cache))
+    wd = m.WilsonDirac(dims, t_antiperiodic=True)
+    wd.load_gauge(U, temporal_gauge=True)
+    srcs = [li.gaussian_spinor(dims, 5100 + r) for r in range(nrhs)]
+    kappas = [0.118, 0.121, 0.124]
+    xs = [np.zeros_like(b) for b in srcs]
+    infos = wd.solve_batch(xs, srcs, kappas, tol=1e-10, inner_precision=prec)
+    for x, b, k, info in zip(xs, srcs, kappas, infos):
+        rel = oracle.true_residual(x, b, U, dims, k, tbc_anti=True)
+        assert info.status == 0 and rel <= 1e-10, (prec, k, info, rel)
+    # the tuned shape (tile 0) now also drives wd_dslash_batch for n = 3
+    fb = wd.field_bytes(prec)
+    fin = wd.new_field(prec, nrhs)
+    for r, s in enumerate(srcs):
+        wd.field_import(fin[r * fb:(r + 1) * fb], s, m.EVEN, prec)
+    fout = wd.new_field(prec, nrhs)
+    wd.dslash_batch(fout, fin, nrhs, m.ODD, True, prec)
+    for r, s in enumerate(srcs):
+        got = wd.download(fout[r * fb:(r + 1) * fb], prec, parity=m.ODD)
+        want = oracle.dslash(s * parity_mask(dims, 0), U, dims, dagger=True, out_parity=1, tbc_anti=True)
+        assert rel_err(got, want) <= TOL[prec], (prec, r)
+    assert "|0 8" in cache.read_text()

@@ -133,3 +133,31 @@ def test_pool_release_and_reallocation(fields):
         assert res.status == 0 and rel <= 1e-10 and res.iters > 2, (res, rel)
     assert srv.stats()["retired"] == 14
     srv.close()
+
+
+@pytest.mark.parametrize("rhs_tile", [-1, 1, 2, 4])
+def test_rhs_tile_shapes(fields, rhs_tile):
+    """Every inner multi-RHS dslash shape (one system per block row, or 1, 2,
+    4 systems per link tile) gives oracle-correct solves, with more requests
+    than slots and staggered tolerances (systems finish at different steps)."""
+    import paper_0911_3191_gb300 as m
+    dims = (8, 8, 8, 16)
+    srv = m.Server(max_slots=3, iters_per_step=4, inner_precision=m.Q16, rhs_tile=rhs_tile, temporal_gauge=True)
+    gid = srv.add_gauge(dims, fields[dims])
+    reqs = []
+    for k in range(5):
+        b = li.gaussian_spinor(dims, 2800 + k)
+        kappa, tol = 0.116 + 0.002 * k, [1e-8, 1e-12][k % 2]
+        reqs.append((srv.submit(gid, b, kappa, tol), b, kappa, tol))
+    done = _drain(srv, [r[0] for r in reqs])
+    for rid, b, kappa, tol in reqs:
+        res, x = done[rid]
+        rel = oracle.true_residual(x, b, fields[dims], dims, kappa)
+        assert res.status == 0 and rel <= tol, (rhs_tile, res, rel)
+    srv.close()
+
+
+def test_rhs_tile_refused():
+    import paper_0911_3191_gb300 as m
+    with pytest.raises(m.WDError):
+        m.Server(rhs_tile=3)
