@@ -78,7 +78,7 @@ FP64_PEAK_TFLOPS = 1.252
 # since the kernel last changed.
 # key: (precision, link reals, lattice, temporal gauge)
 NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", False): 650.13e6, ("f64", 18, "24x24x24x64", True): 525.69e6,
-                     ("q16", 12, "24x24x24x64", True): 90.70e6}
+                     ("q16", 12, "24x24x24x64", True): 90.66e6}
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
 

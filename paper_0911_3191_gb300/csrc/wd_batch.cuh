@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
   for (int k = 0; k < NR; ++k) red[k] = 0.0;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
     R acc[24];
-    dslash_site<DAGGER, TFIX, R8>(g, v, gauge, h, parity, acc);
+    dslash_site<DAGGER, TFIX, R8, Epi::NRED == 0>(g, v, gauge, h, parity, acc);
     e(h, acc, red);
   }
   if constexpr (Epi::NRED > 0) {

@@ -876,6 +876,88 @@ __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, in
   }
 }
 
+// Lower spin rows of reconstruct(): a_lower (+)= S' L_mu(g), assigned when
+// ASSIGN (the first direction of a site).
+template <int MU, int S_, bool ASSIGN, typename R>
+__device__ __forceinline__ void reconstruct_lower(const R (&g)[12], R (&a)[24]) {
+  constexpr int S = (MU == 1) ? -S_ : S_;
+  constexpr R s = (R)S;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R g0r = g[c * 2], g0i = g[c * 2 + 1];
+    const R g1r = g[(3 + c) * 2], g1i = g[(3 + c) * 2 + 1];
+    R l0r, l0i, l1r, l1i;  // rows 2 and 3
+    if constexpr (MU == 0) {
+      l0r = s * g1i; l0i = -s * g1r; l1r = s * g0i; l1i = -s * g0r;
+    } else if constexpr (MU == 1) {
+      l0r = s * g1r; l0i = s * g1i; l1r = -s * g0r; l1i = -s * g0i;
+    } else {
+      l0r = s * g0i; l0i = -s * g0r; l1r = -s * g1i; l1i = s * g1r;
+    }
+    if constexpr (ASSIGN) {
+      a[(6 + c) * 2] = l0r; a[(6 + c) * 2 + 1] = l0i;
+      a[(9 + c) * 2] = l1r; a[(9 + c) * 2 + 1] = l1i;
+    } else {
+      a[(6 + c) * 2] += l0r; a[(6 + c) * 2 + 1] += l0i;
+      a[(9 + c) * 2] += l1r; a[(9 + c) * 2 + 1] += l1i;
+    }
+  }
+}
+
+// The forward and backward hops of one spatial direction together, for
+// unscaled fields (FP64, FP32).  With X = U_mu(x) P_f psi(x + mu) and
+// B = U_mu^dag(x - mu) P_b psi(x - mu) (P_b the projector of opposite sign),
+// the pair adds X + B to the upper spin rows and S' L_mu(X - B) to the lower
+// ones.  One FMA chain forms Y = X + B starting from X, and X - B = 2X - Y:
+// 12 adds fewer than two separate hops; the first direction of a site
+// (FIRST) assigns its 24 values instead of adding them to zeros.
+template <int MU, bool DAGGER, bool R8, bool FIRST, typename R, class In, class G>
+__device__ __forceinline__ void hop_pair(const In& in, const G& gauge, int parity, int h, int np, int nm,
+                                         R (&acc)[24]) {
+  constexpr int SF = DAGGER ? +1 : -1;  // hop()'s S of the forward hop; the backward one has -SF
+  R psi[24];
+  R w = 1;
+  in.load(np, psi);
+  R hf[12];
+  project<MU, SF>(psi, hf);
+  R u[18];
+  gauge.template load_scaled<R8>(parity, MU, h, u, w);
+  R xd[12];  // X, then X - B
+  su3_mul<false>(u, hf, xd);
+  in.load(nm, psi);
+  R hb[12];
+  project<MU, -SF>(psi, hb);
+  gauge.template load_scaled<R8>(1 - parity, MU, nm, u, w);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int k = (sp * 3 + i) * 2;
+      R re = xd[k], im = xd[k + 1];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {  // + conj(U_ji) hb_j, one FMA per real product
+        const int e = j * 3 + i;
+        const R ur = u[2 * e], ui = u[2 * e + 1];
+        const R hr = hb[(sp * 3 + j) * 2], hi = hb[(sp * 3 + j) * 2 + 1];
+        re += ur * hr;
+        re += ui * hi;
+        im += ur * hi;
+        im -= ui * hr;
+      }
+      if constexpr (FIRST) {
+        acc[k] = re;
+        acc[k + 1] = im;
+      } else {
+        acc[k] += re;
+        acc[k + 1] += im;
+      }
+      xd[k] = (R)2 * xd[k] - re;
+      xd[k + 1] = (R)2 * xd[k + 1] - im;
+    }
+  }
+  reconstruct_lower<MU, SF, FIRST>(xd, acc);
+}
+
 // acc = (D in)(site h of parity `parity`), or (D^dag in)(h).  Neighbour
 // indices by offsets from h: in the even-odd order a step in y, z, t moves
 // the index by X/2, XY/2, XYZ/2; a step in x moves it by 0 or 1 depending on
@@ -883,31 +965,50 @@ __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, in
 // TFIX: the links are in the temporal gauge (g.tfix), so the temporal links
 // are 1 off the last time slice (a compile-time variant: the kernels for
 // general links carry no branch for it).
-template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G>
+// PAIR: unscaled fields (FP64, FP32) take the spatial directions as hop pairs
+// (hop_pair); the kernels ask for it only without fused reductions, where the
+// pairs' longer live ranges cost no spills (with reductions, the FP64
+// reliable-update kernel spilled 96 bytes and the solve lost 0.9 ms).
+template <bool DAGGER, bool TFIX, bool R8, bool PAIR = false, typename R, class In, class G>
 __device__ __forceinline__ void dslash_site(const Geom& g, const In& in, const G& gauge, int h, int parity,
                                             R (&acc)[24]) {
   int x, y, z, t;
   site_coords(g, h, parity, x, y, z, t);
+  constexpr bool kPair = PAIR && !(In::kScaled || G::kScaled);
+  if constexpr (!kPair) {
 #pragma unroll
-  for (int k = 0; k < 24; ++k) acc[k] = 0;
+    for (int k = 0; k < 24; ++k) acc[k] = 0;
+  }
   {
     const int xo = x & 1;
     const int np = (x == g.X - 1) ? h - (g.Xh - 1) : h + xo;
     const int nm = (x == 0) ? h + (g.Xh - 1) : h - (xo ^ 1);
-    hop<0, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
-    hop<0, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
+    if constexpr (kPair) {
+      hop_pair<0, DAGGER, R8, true>(in, gauge, parity, h, np, nm, acc);
+    } else {
+      hop<0, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
+      hop<0, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
+    }
   }
   {
     const int np = (y == g.Y - 1) ? h - g.wy : h + g.Xh;
     const int nm = (y == 0) ? h + g.wy : h - g.Xh;
-    hop<1, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
-    hop<1, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
+    if constexpr (kPair) {
+      hop_pair<1, DAGGER, R8, false>(in, gauge, parity, h, np, nm, acc);
+    } else {
+      hop<1, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
+      hop<1, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
+    }
   }
   {
     const int np = (z == g.Z - 1) ? h - g.wz : h + g.XhY;
     const int nm = (z == 0) ? h + g.wz : h - g.XhY;
-    hop<2, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
-    hop<2, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
+    if constexpr (kPair) {
+      hop_pair<2, DAGGER, R8, false>(in, gauge, parity, h, np, nm, acc);
+    } else {
+      hop<2, true, DAGGER, R8>(in, gauge, parity, h, np, false, acc);
+      hop<2, false, DAGGER, R8>(in, gauge, parity, nm, nm, false, acc);
+    }
   }
   {
     const bool top = (t == g.T - 1), bot = (t == 0);
