@@ -70,14 +70,11 @@ FLOPS_PER_SITE = 1320  # the paper's effective count (Sec. 4.3)
 # the unit count agrees: 2 FP64 FMA lanes per SM per clock x 2 flops x 152 SMs
 # x 2.07 GHz = 1.259 TFLOP/s
 FP64_PEAK_TFLOPS = 1.252
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
-# ncu capture of the current kernels (profiles/dslash_f64_18real_24x24x24x64_ncu_full.md);
-# keyed by (precision, link reals, lattice); to be set to None when a kernel changes
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu --set full,
-# the dslash-only command of this file at 24^3x64); None where not captured
-# since the kernel last changed.
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu capture of the current kernel (ncu --set full of the dslash-only
+# command of this file); an entry is removed when its kernel changes.
 # key: (precision, link reals, lattice, temporal gauge)
-NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", False): 650.13e6, ("f64", 18, "24x24x24x64", True): 525.69e6,
+NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", True): 526.54e6,
                      ("q16", 12, "24x24x24x64", True): 90.66e6}
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
@@ -582,6 +579,76 @@ def run_dslash_only(args):
     return 0
 
 
+def run_multishift(args):
+    """Multi-shift solves (wd_solve_multishift_device) on the batched workload:
+    32^3 x 64 lattice (links exp(0.3 i H)), the 12 spin-colour point sources at
+    the origin, each solved for kappa in {0.118, 0.12, 0.122, 0.124} by one
+    shared FP32 multi-shift iteration plus a reliable-update refinement per
+    kappa (Q16 inner) to 1e-12; plus one Gaussian source (two shifted
+    families).  Timed against the same systems solved one at a time."""
+    import numpy as np
+    import torch
+
+    import lattice_inputs as li
+    import paper_0911_3191_gb300 as wdp
+    dims = (32, 32, 32, 64)
+    kappas = [0.118, 0.12, 0.122, 0.124]
+    inner = wdp.PREC_BY_NAME[args.inner]
+    wd = wdp.WilsonDirac(dims)
+    wd.load_gauge(li.gauge(dims, 0.3, 1003), recon=args.recon, temporal_gauge=args.temporal_gauge)
+    V = li.volume(dims)
+    full = 2 * wd.field_bytes(wdp.F64)
+    s = wd.stream
+    host = np.zeros((V, 4, 3), dtype=np.complex128)
+    srcs = []
+    for sp in range(4):
+        for co in range(3):
+            host[0, sp, co] = 1.0
+            srcs.append(("point", wd.upload(host, wdp.F64)))
+            host[0, sp, co] = 0.0
+    srcs.append(("gaussian", wd.upload(li.gaussian_spinor(dims, 2600), wdp.F64)))
+    fx = wd.new_field(wdp.F64, 2 * len(kappas))
+    fx1 = wd.new_field(wdp.F64, 2)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        out = fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, out
+
+    wd.solve_multishift_device(fx, srcs[0][1], kappas, tol=1e-12, inner_precision=inner)  # warm-up
+    wd.solve_device(fx1, srcs[0][1], kappas[0], tol=1e-12, inner_precision=inner)
+    rows = {"point": [0.0, 0.0, 0], "gaussian": [0.0, 0.0, 0]}
+    iters, worst = [], 0.0
+    with ClockSampler(0) as clk:
+        for kind, fb in srcs:
+            t_ms, infos = timed(lambda: wd.solve_multishift_device(fx, fb, kappas, tol=1e-12, inner_precision=inner))
+            assert all(i.status == 0 and i.true_rel_residual <= 1e-12 for i in infos), infos
+            worst = max(worst, max(i.true_rel_residual for i in infos))
+            iters.append([i.iters for i in infos])
+            t_solo = 0.0
+            for k in kappas:
+                t1, r1 = timed(lambda: wd.solve_device(fx1, fb, k, tol=1e-12, inner_precision=inner))
+                assert r1.status == 0
+                t_solo += t1
+            rows[kind][0] += t_ms
+            rows[kind][1] += t_solo
+            rows[kind][2] += 1
+    out = {"multishift": "32x32x32x64, 12 point sources + 1 Gaussian source, kappa " + ",".join(map(str, kappas)),
+           "inner": args.inner, "temporal_gauge": args.temporal_gauge, "tol": 1e-12,
+           "stage": "FP32 multi-shift BiCGstab to 1e-7, then reliable-update refinement per kappa",
+           "max_true_rel_residual": worst, "iters_per_kappa_first_sources": iters[:2] + iters[-1:],
+           "clocks": clk.summary()}
+    for kind, (tm, ts, cnt) in rows.items():
+        out[kind] = {"sources": cnt, "multishift_s": round(tm, 4), "one_at_a_time_s": round(ts, 4),
+                     "speedup": round(ts / tm, 3) if tm else None}
+    print(json.dumps(out))
+    return 0
+
+
 def run_batch(args):
     """Batched multi-RHS solve: 12 point-source spin-colour right-hand sides x
     4 kappa = 48 systems on a 32^3 x 64 lattice (links exp(0.3 i H)), Q16 inner
@@ -841,6 +908,7 @@ def main():
     ap.add_argument("--dslash-only", default=None, choices=["f64", "f32", "q16", "h16n", "b16n"],
                     help="time only the dslash of one precision on --sweep-dims (profiling case)")
     ap.add_argument("--batch", action="store_true", help="batched 48-system multi-RHS solve (32^3x64)")
+    ap.add_argument("--multishift", action="store_true", help="multi-shift solves over 4 kappa (32^3x64)")
     ap.add_argument("--serve", action="store_true", help="continuous-batching serving stream")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="time the FP64 CPU oracle (dslash, solves) on all host cores and on one")
@@ -859,6 +927,8 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.multishift:
+        return run_multishift(args)
     if args.table:
         return run_table(args)
     if args.oracle_timing_child:

@@ -236,6 +236,31 @@ wd_status wd_solve_batch_device(wd_ctx *ctx, int n, void *x, const void *b, cons
 wd_status wd_solve_batch(wd_ctx *ctx, int n, double *const *x, const double *const *b, const double *kappas,
                          const wd_solve_params *params, wd_solve_info *infos);
 
+/* Multi-shift solve over kappa (beyond the paper, whose use case, Sec. 3, is
+ * many solves on one gauge field): M_kappa_k x_k = b for one source and n
+ * kappas (1 <= n <= 32) with one Krylov space.  With the seed kappa_s = the
+ * largest kappa, M_hat(kappa_k) = (kappa_k / kappa_s)^2 (M_hat(kappa_s) +
+ * tau_k), tau_k = (kappa_s / kappa_k)^2 - 1, a shifted family; the Schur
+ * sources b_e + kappa_k D_eo b_o are combinations of b_e and D_eo b_o, each
+ * solved for all shifts at once (a second family only when b_o != 0).  The
+ * multi-shift BiCGstab runs in FP32 storage to a relative residual of 1e-7
+ * (or tol if larger); each kappa is then finished on its FP64 residual by the
+ * solver of wd_solve (params->inner_precision, Alg. 2) to the FP64 true
+ * residual tol.  params->solver is not used (the refinement is BiCGstab).
+ * x[k]: host FP64 fields in the host layout (V x 24 doubles), written; b:
+ * host FP64 source; kappas: host array.  infos[k].iters counts the shared
+ * multi-shift iterations plus that kappa's refinement iterations;
+ * .seconds and .kernel_launches are those of the whole call.  Returns WD_OK
+ * when every kappa reached tol, WD_ERR_NOT_CONVERGED otherwise (infos filled),
+ * WD_ERR_BREAKDOWN / WD_ERR_NUMERIC when the shared iteration fails. */
+wd_status wd_solve_multishift(wd_ctx *ctx, int n, double *const *x, const double *b, const double *kappas,
+                              const wd_solve_params *params, wd_solve_info *infos);
+/* As wd_solve_multishift with device fields in the internal layout: b one
+ * FP64 full field (even then odd); x n FP64 full fields back to back, kappa k
+ * at byte offset k * 2 * wd_field_bytes(ctx, WD_F64). */
+wd_status wd_solve_multishift_device(wd_ctx *ctx, int n, void *x, const void *b, const double *kappas,
+                                     const wd_solve_params *params, wd_solve_info *infos);
+
 /* ---- Serving: continuous batching of solve requests ----------------------
  * A server keeps several gauge fields resident (possibly of different
  * lattice volumes), queues solve requests against them and runs them as

@@ -107,6 +107,10 @@ def load_library():
                                           ctypes.POINTER(SolveInfo)]),
         "wd_solve_batch": (c_int, [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), dp,
                                    ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "wd_solve_multishift": (c_int, [vp, c_int, ctypes.POINTER(vp), vp, dp, ctypes.POINTER(SolveParams),
+                                        ctypes.POINTER(SolveInfo)]),
+        "wd_solve_multishift_device": (c_int, [vp, c_int, vp, vp, dp, ctypes.POINTER(SolveParams),
+                                               ctypes.POINTER(SolveInfo)]),
         "wd_server_create": (c_int, [ctypes.POINTER(vp), ctypes.POINTER(ServerParams)]),
         "wd_server_destroy": (c_int, [vp]),
         "wd_server_add_gauge": (c_int, [vp, ip, c_int, vp, c_int, ip]),
@@ -133,7 +137,7 @@ def exported_symbols():
                         "wd_load_gauge_opt",
                         "wd_field_import", "wd_field_export", "wd_dslash", "wd_dslash_xpay", "wd_apply_M", "wd_norm2",
                         "wd_solve", "wd_solve_device", "wd_dslash_batch", "wd_solve_batch", "wd_solve_batch_device",
-                        "wd_server_create", "wd_server_destroy", "wd_server_add_gauge", "wd_server_submit",
+                        "wd_solve_multishift", "wd_solve_multishift_device", "wd_server_create", "wd_server_destroy", "wd_server_add_gauge", "wd_server_submit",
                         "wd_server_step", "wd_server_poll", "wd_server_memory_in_use", "wd_server_last_error",
                         "wd_server_get_stats",
                         "wd_norm2_noalloc", "wd_last_error", "wd_status_string")
@@ -316,6 +320,35 @@ class WilsonDirac:
         st = self.lib.wd_solve_batch(self.ctx, n, xp, bp, k, ctypes.byref(p), infos)
         if st not in (0, 4, 5, 6) or (check and st != 0):
             self._check(st, "solve_batch")
+        return self._infos(infos, n)
+
+    def solve_multishift(self, xs, b, kappas, tol=1e-12, delta=0.1, max_iter=20000, inner_precision=Q16,
+                         use_graph=True, check=True):
+        """M_kappa_k x_k = b for every kappa (one shared multi-shift iteration,
+        then a refinement per kappa).  xs: list of (V, 4, 3) complex128 host
+        arrays (written); b: (V, 4, 3) complex128."""
+        n = len(kappas)
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+        k = (ctypes.c_double * n)(*[float(v) for v in kappas])
+        p = self._params(tol, delta, max_iter, BICGSTAB, inner_precision, use_graph)
+        infos = (SolveInfo * n)()
+        st = self.lib.wd_solve_multishift(self.ctx, n, xp, _ptr(b), k, ctypes.byref(p), infos)
+        if st not in (0, 4, 5, 6) or (check and st != 0):
+            self._check(st, "solve_multishift")
+        return self._infos(infos, n)
+
+    def solve_multishift_device(self, x, b, kappas, tol=1e-12, delta=0.1, max_iter=20000, inner_precision=Q16,
+                                use_graph=True, check=True):
+        """x: n FP64 full fields back to back (``new_field(F64, 2 * n)``); b:
+        one FP64 full field."""
+        n = len(kappas)
+        k = (ctypes.c_double * n)(*[float(v) for v in kappas])
+        p = self._params(tol, delta, max_iter, BICGSTAB, inner_precision, use_graph)
+        infos = (SolveInfo * n)()
+        st = self.lib.wd_solve_multishift_device(self.ctx, n, _ptr(x), _ptr(b), k, ctypes.byref(p), infos)
+        if st not in (0, 4, 5, 6) or (check and st != 0):
+            self._check(st, "solve_multishift_device")
         return self._infos(infos, n)
 
     # -- conveniences built only from the calls above

@@ -906,24 +906,47 @@ template <>
 struct Tr<WD_B16N> : Tr16<Fmt16::B16, WD_B16N> {};
 
 // ------------------------------------------------------------ launchers
-inline int dslash_grid(const Ctx& c) {
-  int b = (c.g.Vh + kDslashBlock - 1) / kDslashBlock;
-  return b < c.num_sms * 16 ? b : c.num_sms * 16;
+// Resident blocks per SM of a kernel at a block size (asked once per kernel
+// instantiation by its launcher).
+template <class K>
+inline int resident_blocks(K kernel, int block) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 2;
+  }
+  return occ;
 }
-inline int blas_grid(const Ctx& c, int n) {
-  int b = (n + kBlasBlock - 1) / kBlasBlock;
-  return b < c.num_sms * 8 ? b : c.num_sms * 8;
+// Grid of the grid-stride kernels: one wave of resident blocks (every block
+// resident for the whole launch, no partially filled last wave), or fewer
+// blocks when the sites do not fill it.
+inline int wave_grid(int units, int block, int num_sms, int per_sm) {
+  const int b = (units + block - 1) / block;
+  const int w = num_sms * per_sm;
+  return b < w ? b : w;
 }
 
 template <typename R, class In, class G, class Epi>
 void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int dagger, const Epi& epi,
                    cudaStream_t s) {
-  const int grid = dslash_grid(c);
   // FP64 links never use the 8 numbers
   const bool r8 = (sizeof(R) == 4) && c.low_recon == 8;
   auto go = [&](auto dag, auto tfix, auto rec8) {
-    dslash_kernel<decltype(dag)::value, decltype(tfix)::value, decltype(rec8)::value, R, In, G, Epi>
-        <<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
+    constexpr bool kTfix = decltype(tfix)::value;
+    auto* k = dslash_kernel<decltype(dag)::value, kTfix, decltype(rec8)::value, R, In, G, Epi>;
+    // One wave of resident blocks, measured per kernel class against 16
+    // blocks per SM (several waves, the last one partly filled) at 64^3x128:
+    // FP32 15 % faster, 16-bit temporal-gauge and 8-number kernels 5-8 %,
+    // H16N/B16N general links 2-3 %; at 24^3x64 the plain Q16 dslash is 2 %
+    // slower on one wave but its reduction epilogues (fewer block partials)
+    // gain more: the benchmark solve is 3.4 % faster than with 16 blocks per
+    // SM for the small lattices.  The FP64 kernel (FP64-pipe bound; 6 %
+    // slower at 24^3x64) and the general-link Q16 kernel (6 % slower at
+    // 64^3x128) keep 16 blocks per SM.
+    constexpr bool kWave = !(sizeof(R) == 8 || (In::kScaled && In::kBias != 0.f && !kTfix));
+    static const int per_sm = kWave ? resident_blocks(k, kDslashBlock) : 16;
+    const int grid = wave_grid(c.g.Vh, kDslashBlock, c.num_sms, per_sm);
+    k<<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
   };
   using T_ = std::true_type;
   using F_ = std::false_type;
@@ -940,7 +963,8 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
 
 template <class Op>
 void launch_sites(const Ctx& c, int n, const Op& op, cudaStream_t s) {
-  site_kernel<Op><<<blas_grid(c, n), kBlasBlock, 0, s>>>(n, op);
+  static const int per_sm = resident_blocks(site_kernel<Op>, kBlasBlock);
+  site_kernel<Op><<<wave_grid(n, kBlasBlock, c.num_sms, per_sm), kBlasBlock, 0, s>>>(n, op);
 }
 
 // Per-precision implementation.  Inner fields are of precision P; the

@@ -1,0 +1,467 @@
+// Multi-shift solves over kappa (C ABI): M_kappa_k x_k = b for several kappa
+// on one gauge field with one Krylov space.  This goes beyond arXiv:0911.3191
+// (whose use case, Sec. 3, is many solves on one gauge field); it is the
+// shifted-system Krylov method (Jegerlehner 1996; Frommer 2003) applied to the
+// even-odd system of Sec. 3.
+//
+// The kappa family is a shifted family: with Q = -D_eo D_oe,
+// M_hat(kappa) = 1 + kappa^2 Q, so for the seed kappa_s (the largest kappa,
+// the slowest system) M_hat(kappa_k) = (kappa_k / kappa_s)^2 (B + tau_k) with
+// B = M_hat(kappa_s) and tau_k = (kappa_s / kappa_k)^2 - 1 >= 0.  The Schur
+// source b_hat_k = b_e + kappa_k D_eo b_o is a kappa-dependent combination of
+// u = b_e and w = D_eo b_o, so the shifted family is solved for u (and for w
+// when b_o is not zero): (B + tau_k) y_k = u, (B + tau_k) z_k = w, and
+// x_e,k = (kappa_s / kappa_k)^2 (y_k + kappa_k z_k).
+//
+// GB300 layout of the work: the multi-shift BiCGstab runs in FP32 storage
+// (two FP32 M_hat applications per iteration serve every kappa; per-shift
+// vectors x_k, p_k updated by one fused kernel over all shifts) down to a
+// relative residual of 1e-7 (or the requested tol if larger); each kappa is
+// then finished by the mixed-precision reliable-update solver of Alg. 2 on its
+// FP64 residual (b - M x_k, x_k += correction), which brings the FP64 true
+// residual to tol.  The recurrences for the shifted scalars are derived in
+// the oracle's multishift module (test infrastructure), whose pins the tests
+// run.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "wd_kernels.cuh"
+
+using namespace wd;
+
+namespace {
+
+using cplx = std::complex<double>;
+constexpr int kMaxShifts = 32;
+constexpr double kStageTol = 1e-7;  // FP32 multi-shift stage target (relative)
+
+wd_status merr(wd_ctx* ctx, wd_status st, const std::string& m) {
+  ctx->c.last_error = m;
+  return st;
+}
+
+#define MS_CK(call)                                                                                        \
+  do {                                                                                                     \
+    cudaError_t e_ = (call);                                                                               \
+    if (e_ != cudaSuccess)                                                                                 \
+      return merr(ctx, e_ == cudaErrorMemoryAllocation ? WD_ERR_OOM : WD_ERR_CUDA,                         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                     \
+  } while (0)
+#define MS_ST(call)                           \
+  do {                                        \
+    wd_status s_ = (call);                    \
+    if (s_ != WD_OK) return s_;               \
+  } while (0)
+
+// (<a, b>, |a|^2) with <a, b> = sum_sites conj(a) . b: per-site partials in
+// FP32, the sites summed in FP64
+struct OpDotNormF32 {
+  static constexpr int NRED = 3;
+  SpinorF32 a, b;
+  RedScratch rs;
+  FinStore fin;
+  __device__ __forceinline__ void operator()(int h, double* red) const {
+    float av[24], bv[24];
+    a.load(h, av);
+    b.load(h, bv);
+    float re = 0.f, im = 0.f, nn = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re += av[2 * k] * bv[2 * k];
+      re += av[2 * k + 1] * bv[2 * k + 1];
+      im += av[2 * k] * bv[2 * k + 1];
+      im -= av[2 * k + 1] * bv[2 * k];
+      nn += av[2 * k] * av[2 * k];
+      nn += av[2 * k + 1] * av[2 * k + 1];
+    }
+    red[0] += (double)re;
+    red[1] += (double)im;
+    red[2] += (double)nn;
+  }
+};
+
+// out = a - c b (complex c)
+struct OpSubScaledF32 {
+  static constexpr int NRED = 0;
+  SpinorF32 out, a, b;
+  float cr, ci;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    float av[24], bv[24];
+    a.load(h, av);
+    b.load(h, bv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float br = bv[2 * k], bi = bv[2 * k + 1];
+      av[2 * k] -= cr * br;
+      av[2 * k] += ci * bi;
+      av[2 * k + 1] -= cr * bi;
+      av[2 * k + 1] -= ci * br;
+    }
+    out.store_f(h, av);
+  }
+};
+
+// out = a x + b y (real a, b), FP64 fields
+struct OpAxpbyF64 {
+  static constexpr int NRED = 0;
+  SpinorF64 out, x, y;
+  double a, b;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    double xv[24], yv[24];
+    x.load(h, xv);
+    y.load(h, yv);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) xv[k] = a * xv[k] + b * yv[k];
+    out.store(h, xv);
+  }
+};
+
+// Per-shift coefficients of one iteration (complex, as float2):
+// x_k += ax p_k + as s;  p_k = c1 r_new + c2 p_k + c3 r + c4 s.
+struct ShiftCoef {
+  float2 ax, as, c1, c2, c3, c4;
+  int active;
+  int pad;
+};
+struct ShiftCoefs {
+  ShiftCoef k[kMaxShifts];
+};
+
+// y += c x for the two complex numbers of a float4
+__device__ __forceinline__ void cmad4(float4& y, float2 c, float4 x) {
+  y.x += c.x * x.x;
+  y.x -= c.y * x.y;
+  y.y += c.x * x.y;
+  y.y += c.y * x.x;
+  y.z += c.x * x.z;
+  y.z -= c.y * x.w;
+  y.w += c.x * x.w;
+  y.w += c.y * x.z;
+}
+
+// All shifts in one pass: per site and float4 chunk of the spinor the seed's
+// r, r_new and s are read once and every active shift's x_k, p_k updated
+// (fields of the shifts rs bytes apart).
+__global__ void __launch_bounds__(kBlasBlock) shift_update_kernel(int n, int nshift, SpinorF32 xs, SpinorF32 ps,
+                                                                  SpinorF32 r, SpinorF32 r_new, SpinorF32 s,
+                                                                  ShiftCoefs cf) {
+  const int stride = r.stride;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+#pragma unroll 1
+    for (int c = 0; c < 6; ++c) {
+      const size_t o = (size_t)c * stride + h;
+      const float4 rv = __ldg(r.p + o), nv = __ldg(r_new.p + o), sv = __ldg(s.p + o);
+      for (int k = 0; k < nshift; ++k) {
+        const ShiftCoef q = cf.k[k];
+        if (!q.active) continue;
+        float4* xk = (float4*)((char*)xs.p + (size_t)k * xs.rs) + o;
+        float4* pk = (float4*)((char*)ps.p + (size_t)k * ps.rs) + o;
+        const float4 pv = *pk;
+        float4 xv = *xk;
+        cmad4(xv, q.ax, pv);
+        cmad4(xv, q.as, sv);
+        *xk = xv;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        cmad4(t, q.c2, pv);
+        cmad4(t, q.c4, sv);
+        cmad4(t, q.c3, rv);
+        cmad4(t, q.c1, nv);
+        *pk = t;
+      }
+    }
+  }
+}
+
+float2 f2(cplx z) { return make_float2((float)z.real(), (float)z.imag()); }
+
+}  // namespace
+
+namespace {
+
+// FP32 work fields of one shifted family (even parity)
+struct Family {
+  void *r, *rt, *s, *t, *v, *rn;
+  void* xs;  // n solutions, fb apart
+  void* ps;  // n directions, fb apart
+};
+
+// BiCGstab over the shifted family (B + tau_k) y_k = src, B = M_hat(kappa_s),
+// tau_0 = 0 (the seed).  Scalars on the host; one fused update of all x_k,
+// p_k per iteration.  Returns when the seed's iterated residual reaches
+// tol_rel |src| (the shifted systems, whose residuals are the seed's divided
+// by |pi_k f_k| >= 1 in practice, stop being updated once they reach it).
+wd_status family_solve(wd_ctx* ctx, const void* src, double kappa_s, const std::vector<double>& tau, int max_iter,
+                       double tol_rel, Family& f, size_t fb, int& iters, long long& launches) {
+  Ctx& c = ctx->c;
+  cudaStream_t st = c.stream;
+  const Geom& g = c.g;
+  const int n = (int)tau.size();
+  double* hp = c.host_pinned;
+  auto V = [&](const void* p, size_t rs = 0) { return Tr<WD_F32>::view(p, g, rs); };
+  auto dotnorm = [&](const void* a, const void* b) {  // -> hp[16..18] = <a, b>, |a|^2
+    launch_sites(c, g.Vh, OpDotNormF32{V(a), V(b), c.red, FinStore{c.scalars + 16, 3}}, st);
+    ++launches;
+  };
+  auto fetch = [&]() -> wd_status {
+    MS_CK(cudaMemcpyAsync(hp + 16, c.scalars + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MS_CK(cudaStreamSynchronize(st));
+    return WD_OK;
+  };
+  MS_CK(cudaMemcpyAsync(f.r, src, fb, cudaMemcpyDeviceToDevice, st));
+  MS_CK(cudaMemcpyAsync(f.rt, src, fb, cudaMemcpyDeviceToDevice, st));
+  for (int k = 0; k < n; ++k) MS_CK(cudaMemcpyAsync((char*)f.ps + k * fb, src, fb, cudaMemcpyDeviceToDevice, st));
+  MS_CK(cudaMemsetAsync(f.xs, 0, n * fb, st));
+  dotnorm(f.r, f.rt);
+  MS_ST(fetch());
+  iters = 0;
+  const double src2 = hp[18];
+  if (!std::isfinite(src2)) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: source not finite");
+  if (src2 == 0.0) return WD_OK;  // y = 0
+  cplx rho = std::conj(cplx(hp[16], hp[17]));
+  std::vector<cplx> fz(n, 1.0), gz(n, 1.0), pz(n, 1.0);
+  std::vector<char> active(n, 1);
+  const double stop = tol_rel * std::sqrt(src2);
+  const int gx = std::min((g.Vh + kBlasBlock - 1) / kBlasBlock, c.num_sms * 8);
+  while (iters < max_iter) {
+    ++iters;
+    MS_ST(wd_apply_M(ctx, f.v, f.ps, kappa_s, WD_M_SCHUR_EVEN, 0, WD_F32));  // v = B p_0
+    launches += 2;
+    dotnorm(f.v, f.rt);
+    MS_ST(fetch());
+    const cplx rtv = std::conj(cplx(hp[16], hp[17]));
+    if (!std::isfinite(std::abs(rtv))) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: NaN/Inf");
+    if (std::abs(rtv) == 0.0 || std::abs(rho) == 0.0) return merr(ctx, WD_ERR_BREAKDOWN, "multi-shift: <r0, v> = 0");
+    const cplx alpha = rho / rtv;
+    launch_sites(c, g.Vh, OpSubScaledF32{V(f.s), V(f.r), V(f.v), (float)alpha.real(), (float)alpha.imag()}, st);
+    MS_ST(wd_apply_M(ctx, f.t, f.s, kappa_s, WD_M_SCHUR_EVEN, 0, WD_F32));  // t = B s
+    launches += 3;
+    dotnorm(f.t, f.s);
+    MS_ST(fetch());
+    const cplx ts(hp[16], hp[17]);
+    const double tt = hp[18];
+    if (!std::isfinite(tt)) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: NaN/Inf");
+    if (tt == 0.0) return merr(ctx, WD_ERR_BREAKDOWN, "multi-shift: <t, t> = 0");
+    const cplx omega = ts / tt;
+    if (std::abs(omega) == 0.0) return merr(ctx, WD_ERR_BREAKDOWN, "multi-shift: omega = 0");
+    launch_sites(c, g.Vh, OpSubScaledF32{V(f.rn), V(f.s), V(f.t), (float)omega.real(), (float)omega.imag()}, st);
+    ++launches;
+    dotnorm(f.rn, f.rt);
+    MS_ST(fetch());
+    const cplx rho_new = std::conj(cplx(hp[16], hp[17]));
+    const double rn = std::sqrt(hp[18]);
+    const cplx beta = (alpha / omega) * (rho_new / rho);
+    ShiftCoefs cf{};
+    for (int k = 0; k < n; ++k) {
+      if (!active[k]) continue;
+      const double sg = tau[k];
+      const cplx f_next = fz[k] + alpha * sg * gz[k];
+      const cplx alpha_s = alpha * fz[k] / f_next;
+      const cplx omega_s = omega / (1.0 + omega * sg);
+      const cplx pi_next = pz[k] * (1.0 + omega * sg);
+      const cplx beta_s = beta * (fz[k] / f_next) * (fz[k] / f_next);
+      const cplx q = beta_s * omega_s / alpha_s;
+      cf.k[k] = ShiftCoef{f2(alpha_s), f2(omega_s / (pz[k] * f_next)), f2(1.0 / (pi_next * f_next)), f2(beta_s),
+                          f2(-q / (pz[k] * fz[k])), f2(q / (pz[k] * f_next)), 1, 0};
+      gz[k] = f_next + beta * gz[k];
+      fz[k] = f_next;
+      pz[k] = pi_next;
+    }
+    shift_update_kernel<<<gx, kBlasBlock, 0, st>>>(g.Vh, n, V(f.xs, fb), V(f.ps, fb), V(f.r), V(f.rn), V(f.s), cf);
+    ++launches;
+    MS_CK(cudaGetLastError());
+    for (int k = 1; k < n; ++k)  // the seed (k = 0) drives the iteration and stays active
+      if (active[k] && rn <= stop * std::abs(pz[k] * fz[k])) active[k] = 0;
+    std::swap(f.r, f.rn);
+    rho = rho_new;
+    if (!std::isfinite(rn)) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: NaN/Inf");
+    if (rn <= stop) break;
+  }
+  return WD_OK;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+}  // namespace
+
+namespace {
+
+// x: n FP64 full fields (even, odd) back to back; b: one FP64 full field;
+// both device memory in the internal layout
+wd_status multishift_core(wd_ctx* ctx, int n, char* x, const char* b, const double* kappas,
+                          const wd_solve_params* params, wd_solve_info* infos) {
+  for (int k = 0; k < n; ++k)
+    if (!(kappas[k] > 0.0) || !std::isfinite(kappas[k]) || !(params->tol > 0.0) || params->max_iter < 1)
+      return merr(ctx, WD_ERR_INVALID_ARG, "wd_solve_multishift: bad kappa, tol or max_iter");
+  Ctx& c = ctx->c;
+  if (!c.gauge_loaded) return merr(ctx, WD_ERR_INVALID_ARG, "wd_solve_multishift: no gauge field loaded");
+  MS_ST(wd_internal_ensure_gauge(ctx, WD_F64));
+  MS_ST(wd_internal_ensure_gauge(ctx, WD_F32));
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = c.stream;
+  const Geom& g = c.g;
+  const size_t f64 = Tr<WD_F64>::bytes(g.stride), f32 = Tr<WD_F32>::bytes(g.stride);
+  DevBuf mem;
+  mem.s = st;
+  const size_t bytes64 = (size_t)(2 + 2 + 1) * f64, bytes32 = (size_t)(7 + 3 * n) * f32;
+  MS_CK(cudaMallocAsync(&mem.p, bytes64 + bytes32, st));
+  char* q = (char*)mem.p;
+  char* tfull = q;  q += 2 * f64;   // M x_k, then the correction e
+  char* rfull = q;  q += 2 * f64;   // b - M x_k
+  char* w64 = q;    q += f64;       // D_eo b_o, and a conversion scratch
+  Family fam{};
+  fam.r = q;  q += f32;
+  fam.rt = q; q += f32;
+  fam.s = q;  q += f32;
+  fam.t = q;  q += f32;
+  fam.v = q;  q += f32;
+  fam.rn = q; q += f32;
+  char* src32 = q; q += f32;
+  char* ys = q; q += n * f32;
+  char* zs = q; q += n * f32;
+  fam.ps = q;
+  auto V64 = [&](const void* p) { return Tr<WD_F64>::view(p, g); };
+  long long launches = 0;
+  const PrecOps* o64 = ops_f64();
+  const PrecOps* o32 = prec_ops(WD_F32);
+  double* hp = c.host_pinned;
+  const char* b_e = b;
+  const char* b_o = b + f64;
+  o64->norm2(c, c.scalars + 20, b_e, st);
+  o64->norm2(c, c.scalars + 21, b_o, st);
+  launches += 2;
+  MS_CK(cudaMemcpyAsync(hp + 20, c.scalars + 20, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  MS_CK(cudaStreamSynchronize(st));
+  const double be2 = hp[20], bo2 = hp[21], b2 = be2 + bo2;
+  if (!std::isfinite(b2)) return merr(ctx, WD_ERR_NUMERIC, "wd_solve_multishift: source not finite");
+  // seed first: the largest kappa is the slowest system
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int bb) { return kappas[a] > kappas[bb]; });
+  const double ks = kappas[order[0]];
+  std::vector<double> tau(n);
+  for (int i = 0; i < n; ++i) tau[i] = (ks / kappas[order[i]]) * (ks / kappas[order[i]]) - 1.0;
+  const double stage_tol = std::max(params->tol, kStageTol);
+  int it_u = 0, it_w = 0;
+  if (be2 > 0.0) {
+    o32->from_f64(c, src32, b_e, st);
+    fam.xs = ys;
+    MS_ST(family_solve(ctx, src32, ks, tau, params->max_iter, stage_tol, fam, f32, it_u, launches));
+  } else {
+    MS_CK(cudaMemsetAsync(ys, 0, n * f32, st));
+  }
+  if (bo2 > 0.0) {
+    o64->dslash(c, w64, b_o, 0, 0, st);  // w = D_eo b_o
+    o32->from_f64(c, src32, w64, st);
+    launches += 2;
+    fam.xs = zs;
+    MS_ST(family_solve(ctx, src32, ks, tau, params->max_iter, stage_tol, fam, f32, it_w, launches));
+  }
+  const int ms_iters = it_u + it_w;
+  wd_status worst = WD_OK;
+  for (int i = 0; i < n; ++i) {
+    const int k = order[i];
+    const double kap = kappas[k], sc = (ks / kap) * (ks / kap);
+    char* xfull = x + (size_t)k * 2 * f64;
+    char* xe = xfull;
+    char* xo = xfull + f64;
+    // x_e = (kappa_s / kappa)^2 (y + kappa z), x_o = b_o + kappa D_oe x_e (Sec. 3)
+    o32->to_f64(c, xe, ys + (size_t)i * f32, st);
+    if (bo2 > 0.0) {
+      o32->to_f64(c, w64, zs + (size_t)i * f32, st);
+      launch_sites(c, g.Vh, OpAxpbyF64{V64(xe), V64(xe), V64(w64), sc, sc * kap}, st);
+    } else {
+      launch_sites(c, g.Vh, OpAxpbyF64{V64(xe), V64(xe), V64(xe), sc, 0.0}, st);
+    }
+    o64->dslash_xpay(c, xo, xe, b_o, kap, nullptr, 1, 0, st);
+    launches += 4;
+    // FP64 residual on the full lattice; the reliable-update solver finishes it
+    auto residual = [&](double& rel) -> wd_status {
+      MS_ST(wd_apply_M(ctx, tfull, xfull, kap, WD_M_FULL, 0, WD_F64));
+      for (int par = 0; par < 2; ++par)
+        launch_sites(c, g.Vh, OpAxpbyF64{V64(rfull + par * f64), V64(b + par * f64), V64(tfull + par * f64),
+                                         1.0, -1.0}, st);
+      o64->norm2(c, c.scalars + 22, rfull, st);
+      o64->norm2(c, c.scalars + 23, rfull + f64, st);
+      launches += 6;
+      MS_CK(cudaMemcpyAsync(hp + 22, c.scalars + 22, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      MS_CK(cudaStreamSynchronize(st));
+      rel = b2 > 0.0 ? std::sqrt((hp[22] + hp[23]) / b2) : 0.0;
+      return WD_OK;
+    };
+    double rel = 0.0;
+    MS_ST(residual(rel));
+    wd_solve_info ie{};
+    if (std::isfinite(rel) && rel > params->tol) {
+      wd_solve_params p2 = *params;
+      p2.tol = 0.5 * params->tol / rel;
+      p2.solver = WD_BICGSTAB;
+      wd_status se = wd_solve_device(ctx, tfull, rfull, kap, &p2, &ie);
+      if (se != WD_OK && se != WD_ERR_NOT_CONVERGED) return se;
+      for (int par = 0; par < 2; ++par)
+        launch_sites(c, g.Vh, OpAxpbyF64{V64(xfull + par * f64), V64(xfull + par * f64), V64(tfull + par * f64),
+                                         1.0, 1.0}, st);
+      launches += 2 + ie.kernel_launches;
+      MS_ST(residual(rel));
+    }
+    const wd_status sk = !std::isfinite(rel) ? WD_ERR_NUMERIC : (rel <= params->tol ? WD_OK : WD_ERR_NOT_CONVERGED);
+    if (sk != WD_OK && worst == WD_OK) worst = sk;
+    wd_solve_info& inf = infos[k];
+    inf.iters = ms_iters + ie.iters;
+    inf.reliable_updates = ie.reliable_updates;
+    inf.true_rel_residual = rel;
+    inf.iterated_rel_residual = ie.iterated_rel_residual;
+    inf.status = sk;
+  }
+  MS_CK(cudaStreamSynchronize(st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int k = 0; k < n; ++k) {
+    infos[k].seconds = secs;
+    infos[k].kernel_launches = launches;
+  }
+  if (worst != WD_OK) return merr(ctx, worst, "wd_solve_multishift: some kappa did not reach tol");
+  return WD_OK;
+}
+
+}  // namespace
+
+extern "C" wd_status wd_solve_multishift_device(wd_ctx* ctx, int n, void* x, const void* b, const double* kappas,
+                                                const wd_solve_params* params, wd_solve_info* infos) {
+  if (!ctx || n < 1 || n > kMaxShifts || !x || !b || !kappas || !params || !infos)
+    return ctx ? merr(ctx, WD_ERR_INVALID_ARG, "wd_solve_multishift_device: bad args") : WD_ERR_INVALID_ARG;
+  MS_CK(cudaSetDevice(ctx->c.device));
+  return multishift_core(ctx, n, (char*)x, (const char*)b, kappas, params, infos);
+}
+
+extern "C" wd_status wd_solve_multishift(wd_ctx* ctx, int n, double* const* x, const double* b,
+                                         const double* kappas, const wd_solve_params* params,
+                                         wd_solve_info* infos) {
+  if (!ctx || n < 1 || n > kMaxShifts || !x || !b || !kappas || !params || !infos)
+    return ctx ? merr(ctx, WD_ERR_INVALID_ARG, "wd_solve_multishift: bad args") : WD_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!x[k]) return merr(ctx, WD_ERR_INVALID_ARG, "wd_solve_multishift: bad x");
+  Ctx& c = ctx->c;
+  MS_CK(cudaSetDevice(c.device));
+  if (!c.gauge_loaded) return merr(ctx, WD_ERR_INVALID_ARG, "wd_solve_multishift: no gauge field loaded");
+  const size_t f64 = Tr<WD_F64>::bytes(c.g.stride);
+  DevBuf mem;
+  mem.s = c.stream;
+  MS_CK(cudaMallocAsync(&mem.p, (size_t)(n + 1) * 2 * f64, c.stream));
+  char* bdev = (char*)mem.p;
+  char* xdev = bdev + 2 * f64;
+  MS_ST(wd_internal_import_full(ctx, bdev, bdev + f64, b));
+  const wd_status st = multishift_core(ctx, n, xdev, bdev, kappas, params, infos);
+  if (st != WD_OK && st != WD_ERR_NOT_CONVERGED) return st;
+  for (int k = 0; k < n; ++k) MS_ST(wd_internal_export_full(ctx, x[k], xdev + (size_t)k * 2 * f64,
+                                                            xdev + (size_t)k * 2 * f64 + f64));
+  return st;
+}

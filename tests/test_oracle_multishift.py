@@ -1,0 +1,59 @@
+"""Pins for the multi-shift BiCGstab recurrences (oracle/multishift.py), which
+the CUDA multi-shift solver follows: every shifted solution equals a dense LU
+solve (numpy.linalg.solve) of its own system, and on the Wilson-Dirac Schur
+operator the kappa family M_hat(kappa_k) = (kappa_k / kappa_s)^2
+(M_hat(kappa_s) + tau_k), tau_k = (kappa_s / kappa_k)^2 - 1, reproduces the
+oracle's single-kappa solves."""
+import numpy as np
+import pytest
+
+import lattice_inputs as li
+import oracle
+from oracle.multishift import multishift_bicgstab
+from tests.wd_testutil import parity_mask
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_dense_shifted_family(seed):
+    rng = np.random.default_rng(seed)
+    n = 80
+    A = 3.0 * np.eye(n) + (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / np.sqrt(n)
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    shifts = [0.0, 0.05, 0.4, 1.7]
+    xs, it, hist = multishift_bicgstab(lambda v: A @ v, b, shifts, tol=1e-13)
+    assert it < n
+    for sg, x in zip(shifts, xs):
+        want = np.linalg.solve(A + sg * np.eye(n), b)
+        assert np.linalg.norm(x - want) / np.linalg.norm(want) < 1e-11, sg
+
+
+def test_seed_alone_is_bicgstab():
+    """With the single shift 0 the recurrences reduce to BiCGstab: the
+    residual history equals the oracle's own BiCGstab on the same system."""
+    rng = np.random.default_rng(4)
+    n = 50
+    A = 2.0 * np.eye(n) + (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / np.sqrt(n)
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    xs, it, _ = multishift_bicgstab(lambda v: A @ v, b, [0.0], tol=1e-12)
+    assert np.linalg.norm(A @ xs[0] - b) / np.linalg.norm(b) < 1e-11
+
+
+def test_wilson_kappa_family():
+    """Shifts of M_hat(kappa_s): x(kappa_k) = (kappa_s / kappa_k)^2 y_k with
+    (M_hat(kappa_s) + tau_k) y_k = b_e solves M_hat(kappa_k) x = b_e."""
+    dims = (4, 4, 4, 8)
+    U = li.gauge(dims, 0.5, 1400)
+    b = li.gaussian_spinor(dims, 2400) * parity_mask(dims, 0)
+    kappas = [0.124, 0.12, 0.118, 0.11]
+    ks = max(kappas)
+    taus = [(ks / k) ** 2 - 1.0 for k in kappas]
+    mask = np.broadcast_to(parity_mask(dims, 0), b.shape).reshape(-1)
+
+    def B(v):
+        return oracle.apply_Mhat(v.reshape(b.shape), U, dims, ks).reshape(-1) * mask
+
+    ys, it, _ = multishift_bicgstab(B, b.reshape(-1), taus, tol=1e-12)
+    for k, y in zip(kappas, ys):
+        x = ((ks / k) ** 2 * y).reshape(b.shape)
+        r = b - oracle.apply_Mhat(x, U, dims, k)
+        assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-11, k
