@@ -471,6 +471,13 @@ struct EpiRelupBicg {
 };
 
 // --------------------------------------------------------------- kernels
+// Programmatic dependent launch: the solver's kernels are launched with the
+// programmatic-serialization attribute, so a kernel's blocks are scheduled
+// while its predecessor drains; each waits here, before it touches memory,
+// until the predecessor has completed and its writes are visible.  For a
+// launch without the attribute the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Resident blocks per SM the register allocation is held to (chosen from
 // ptxas register and spill counts): the FP32 and 16-bit kernels are
 // memory-latency bound and want warps, the fused-reduction epilogues need a
@@ -488,6 +495,7 @@ struct DslashOccupancy {
 template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G, class Epi>
 __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRED, TFIX, R8>::kMinBlocks))
     dslash_kernel(Geom g, In in, G gauge, int parity, Epi epi) {
+  pdl_wait();
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   double red[NR];
 #pragma unroll
@@ -502,6 +510,7 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
 
 template <class Op>
 __global__ void __launch_bounds__(kBlasBlock) site_kernel(int n, Op op) {
+  pdl_wait();
   constexpr int NR = Op::NRED > 0 ? Op::NRED : 1;
   double red[NR];
 #pragma unroll
@@ -917,6 +926,23 @@ inline int resident_blocks(K kernel, int block) {
   }
   return occ;
 }
+// Launch with the programmatic-serialization attribute (see pdl_wait); on a
+// stream being captured it becomes a programmatic edge of the graph.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Grid of the grid-stride kernels: one wave of resident blocks (every block
 // resident for the whole launch, no partially filled last wave), or fewer
 // blocks when the sites do not fill it.
@@ -946,7 +972,7 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
     constexpr bool kWave = !(sizeof(R) == 8 || (In::kScaled && In::kBias != 0.f && !kTfix));
     static const int per_sm = kWave ? resident_blocks(k, kDslashBlock) : 16;
     const int grid = wave_grid(c.g.Vh, kDslashBlock, c.num_sms, per_sm);
-    k<<<grid, kDslashBlock, 0, s>>>(c.g, in, gauge, parity, epi);
+    launch_pdl(k, grid, kDslashBlock, s, c.g, in, gauge, parity, epi);
   };
   using T_ = std::true_type;
   using F_ = std::false_type;
@@ -964,7 +990,7 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
 template <class Op>
 void launch_sites(const Ctx& c, int n, const Op& op, cudaStream_t s) {
   static const int per_sm = resident_blocks(site_kernel<Op>, kBlasBlock);
-  site_kernel<Op><<<wave_grid(n, kBlasBlock, c.num_sms, per_sm), kBlasBlock, 0, s>>>(n, op);
+  launch_pdl(site_kernel<Op>, wave_grid(n, kBlasBlock, c.num_sms, per_sm), kBlasBlock, s, n, op);
 }
 
 // Per-precision implementation.  Inner fields are of precision P; the
