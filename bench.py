@@ -74,8 +74,8 @@ FP64_PEAK_TFLOPS = 1.252
 # the ncu capture of the current kernel (ncu --set full of the dslash-only
 # command of this file); an entry is removed when its kernel changes.
 # key: (precision, link reals, lattice, temporal gauge)
-NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", True): 526.54e6,
-                     ("q16", 12, "24x24x24x64", True): 91.08e6}
+NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", True): 526.07e6,
+                     ("q16", 12, "24x24x24x64", True): 90.98e6}
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
 
