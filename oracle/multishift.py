@@ -38,6 +38,8 @@ def multishift_bicgstab(apply_A, b, shifts, tol=1e-10, maxiter=10000):
     its residual |r^s| <= tol |b|; the loop ends when all have."""
     b = np.asarray(b, dtype=np.complex128)
     shifts = [float(s) for s in shifts]
+    if not shifts or shifts[0] != 0.0:
+        raise ValueError("shifts[0] must be 0: the seed system drives the iteration")
     n = len(shifts)
     bnorm = np.linalg.norm(b)
     xs = [np.zeros_like(b) for _ in range(n)]

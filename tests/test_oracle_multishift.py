@@ -57,3 +57,37 @@ def test_wilson_kappa_family():
         x = ((ks / k) ** 2 * y).reshape(b.shape)
         r = b - oracle.apply_Mhat(x, U, dims, k)
         assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-11, k
+
+
+def test_wilson_general_source_two_families():
+    """The combination the CUDA multi-shift solver uses for a general source:
+    y_k, z_k solve (M_hat(kappa_s) + tau_k) (.) = b_e, D_eo b_o; then
+    x_e = (kappa_s / kappa_k)^2 (y_k + kappa_k z_k), x_o = b_o + kappa_k D_oe x_e
+    solves M_kappa_k x = b on the full lattice."""
+    dims = (4, 4, 4, 8)
+    U = li.gauge(dims, 0.5, 1401)
+    b = li.gaussian_spinor(dims, 2401)
+    even = np.broadcast_to(parity_mask(dims, 0), b.shape)
+    odd = np.broadcast_to(parity_mask(dims, 1), b.shape)
+    b_e, b_o = b * even, b * odd
+    kappas = [0.124, 0.12, 0.115]  # the seed (largest kappa, shift 0) first
+    ks = max(kappas)
+    taus = [(ks / k) ** 2 - 1.0 for k in kappas]
+    m = even.reshape(-1)
+
+    def B(v):
+        return oracle.apply_Mhat(v.reshape(b.shape), U, dims, ks).reshape(-1) * m
+
+    w = oracle.dslash(b_o, U, dims, out_parity=0)  # D_eo b_o
+    ys, _, _ = multishift_bicgstab(B, b_e.reshape(-1), taus, tol=1e-13)
+    zs, _, _ = multishift_bicgstab(B, w.reshape(-1), taus, tol=1e-13)
+    for k, y, z in zip(kappas, ys, zs):
+        x_e = ((ks / k) ** 2 * (y + k * z)).reshape(b.shape)
+        x_o = b_o + k * oracle.dslash(x_e, U, dims, out_parity=1)
+        x = x_e + x_o
+        assert oracle.true_residual(x, b, U, dims, k) < 1e-11, k
+
+
+def test_seed_must_come_first():
+    with pytest.raises(ValueError):
+        multishift_bicgstab(lambda v: v, np.ones(4), [0.1, 0.0])
