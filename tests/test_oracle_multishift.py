@@ -91,3 +91,31 @@ def test_wilson_general_source_two_families():
 def test_seed_must_come_first():
     with pytest.raises(ValueError):
         multishift_bicgstab(lambda v: v, np.ones(4), [0.1, 0.0])
+
+
+@pytest.mark.parametrize("mutation", [
+    ("beta_s = beta * (f[k] / f_next) ** 2", "beta_s = beta"),
+    ("omega_s = omega / (1.0 + omega * sig)", "omega_s = omega"),
+    ("pi[k] = pi_next", "pi[k] = pi[k]"),
+    ("f_next = f[k] + alpha * sig * g[k]", "f_next = f[k] + alpha * sig * f[k]"),
+])
+def test_planted_mistakes_fail_the_dense_pin(mutation):
+    """A copy of the recurrences with one plausible mistake planted no longer
+    matches the dense LU solves of the shifted systems."""
+    import os
+    import types
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "multishift.py")).read()
+    old, new = mutation
+    assert src.count(old) == 1
+    mod = types.ModuleType("multishift_mutant")
+    exec(compile(src.replace(old, new), "multishift_mutant", "exec"), mod.__dict__)
+    rng = np.random.default_rng(5)
+    n = 60
+    A = 3.0 * np.eye(n) + (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))) / np.sqrt(n)
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    shifts = [0.0, 0.4, 1.7]
+    with np.errstate(all="ignore"):
+        xs, _, _ = mod.multishift_bicgstab(lambda v: A @ v, b, shifts, tol=1e-12, maxiter=200)
+    errs = [np.linalg.norm(x - np.linalg.solve(A + s * np.eye(n), b)) / np.linalg.norm(b)
+            for s, x in zip(shifts, xs)]
+    assert not all(np.isfinite(e) and e < 1e-8 for e in errs), errs
