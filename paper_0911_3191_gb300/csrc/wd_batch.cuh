@@ -144,6 +144,7 @@ constexpr size_t tile_link_bytes() {
 template <bool DAGGER, typename R, class In, class G, class Epi, int TR>
 __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G gauge, int parity, Epi epi,
                                                               BatchArgs ba) {
+  pdl_wait();
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* lk = reinterpret_cast<R*>(smem_raw);
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
 template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G, class Epi>
 __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRED, TFIX, R8>::kMinBlocks))
     dslash_rhs_kernel(Geom g, In in, G gauge, int parity, Epi epi, BatchArgs ba) {
+  pdl_wait();
   constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
   const int i = blockIdx.y;
   int r = i;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
 // Site kernel over a batch: blockIdx.y is the right-hand side.
 template <class Op>
 __global__ void __launch_bounds__(kBlasBlock) site_batch_kernel(int n, Op op, BatchArgs ba) {
+  pdl_wait();
   constexpr int NR = Op::NRED > 0 ? Op::NRED : 1;
   const int r = blockIdx.y;
   double red[NR];
@@ -281,6 +284,7 @@ __global__ void __launch_bounds__(kBlasBlock) site_batch_kernel(int n, Op op, Ba
 template <int NR, class Fin>
 __global__ void __launch_bounds__(128) batch_finalize_kernel(BatchArgs ba, int nblk, Fin fin, BatchCtl* bc,
                                                              int which, int set_update) {
+  pdl_wait();
   const int r = blockIdx.x;
   double s[NR];
 #pragma unroll
@@ -351,8 +355,8 @@ void launch_dslash_mrhs(const Geom& g, const BatchLaunch& bl, const In& in, cons
   if (sizeof(R) == 8 || bl.tr == 0) {
     const dim3 gr(grid, bl.nrhs);
     auto go = [&](auto dag, auto tfix, auto rec8) {
-      dslash_rhs_kernel<decltype(dag)::value, decltype(tfix)::value, decltype(rec8)::value, R, In, G, Epi>
-          <<<gr, kDslashBlock, 0, s>>>(g, in, gauge, parity, epi, ba);
+      launch_pdl(dslash_rhs_kernel<decltype(dag)::value, decltype(tfix)::value, decltype(rec8)::value, R, In, G, Epi>,
+                 gr, dim3(kDslashBlock), 0, s, g, in, gauge, parity, epi, ba);
     };
     using T_ = std::true_type;
     using F_ = std::false_type;
@@ -371,11 +375,11 @@ void launch_dslash_mrhs(const Geom& g, const BatchLaunch& bl, const In& in, cons
 #define WD_MRHS_CASE(TRV)                                                                                   \
   case TRV:                                                                                                 \
     if (dagger)                                                                                             \
-      dslash_mrhs_kernel<true, R, In, G, Epi, TRV><<<grid, dim3(32, TRV), smem, s>>>(g, in, gauge, parity,    \
-                                                                                     epi, ba);              \
+      launch_pdl(dslash_mrhs_kernel<true, R, In, G, Epi, TRV>, dim3(grid), dim3(32, TRV), smem, s, g, in,    \
+                 gauge, parity, epi, ba);                                                                   \
     else                                                                                                    \
-      dslash_mrhs_kernel<false, R, In, G, Epi, TRV><<<grid, dim3(32, TRV), smem, s>>>(g, in, gauge, parity,   \
-                                                                                      epi, ba);             \
+      launch_pdl(dslash_mrhs_kernel<false, R, In, G, Epi, TRV>, dim3(grid), dim3(32, TRV), smem, s, g, in,   \
+                 gauge, parity, epi, ba);                                                                   \
     break;
   switch (tr) {
     WD_MRHS_CASE(1)
@@ -388,13 +392,13 @@ void launch_dslash_mrhs(const Geom& g, const BatchLaunch& bl, const In& in, cons
 
 template <class Op>
 void launch_sites_batch(const Geom& g, const BatchLaunch& bl, const Op& op, const BatchArgs& ba, cudaStream_t s) {
-  site_batch_kernel<Op><<<dim3(bl.blas_gx, bl.nrhs), kBlasBlock, 0, s>>>(g.Vh, op, ba);
+  launch_pdl(site_batch_kernel<Op>, dim3(bl.blas_gx, bl.nrhs), dim3(kBlasBlock), 0, s, g.Vh, op, ba);
 }
 
 template <int NR, class Fin>
 void launch_finalize(const BatchLaunch& bl, const BatchArgs& ba, int nblk, const Fin& fin, BatchCtl* bc, int which,
                      int set_update, cudaStream_t s) {
-  batch_finalize_kernel<NR, Fin><<<bl.nrhs, 128, 0, s>>>(ba, nblk, fin, bc, which, set_update);
+  launch_pdl(batch_finalize_kernel<NR, Fin>, dim3(bl.nrhs), dim3(128), 0, s, ba, nblk, fin, bc, which, set_update);
 }
 
 // Fields of a batched solve: one allocation per field kind, system r's field

@@ -929,11 +929,12 @@ inline int resident_blocks(K kernel, int block) {
 // Launch with the programmatic-serialization attribute (see pdl_wait); on a
 // stream being captured it becomes a programmatic edge of the graph.
 template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -972,7 +973,7 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
     constexpr bool kWave = !(sizeof(R) == 8 || (In::kScaled && In::kBias != 0.f && !kTfix));
     static const int per_sm = kWave ? resident_blocks(k, kDslashBlock) : 16;
     const int grid = wave_grid(c.g.Vh, kDslashBlock, c.num_sms, per_sm);
-    launch_pdl(k, grid, kDslashBlock, s, c.g, in, gauge, parity, epi);
+    launch_pdl(k, dim3(grid), dim3(kDslashBlock), 0, s, c.g, in, gauge, parity, epi);
   };
   using T_ = std::true_type;
   using F_ = std::false_type;
@@ -990,7 +991,7 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
 template <class Op>
 void launch_sites(const Ctx& c, int n, const Op& op, cudaStream_t s) {
   static const int per_sm = resident_blocks(site_kernel<Op>, kBlasBlock);
-  launch_pdl(site_kernel<Op>, wave_grid(n, kBlasBlock, c.num_sms, per_sm), kBlasBlock, s, n, op);
+  launch_pdl(site_kernel<Op>, dim3(wave_grid(n, kBlasBlock, c.num_sms, per_sm)), dim3(kBlasBlock), 0, s, n, op);
 }
 
 // Per-precision implementation.  Inner fields are of precision P; the
