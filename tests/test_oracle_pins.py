@@ -383,3 +383,40 @@ def test_su3_8number_singularity_flagged():
     assert oracle.su3_to8(np.eye(3, dtype=np.complex128))[1]
     D = np.diag(np.exp(1j * np.array([0.3, -0.5, 0.2])))
     assert oracle.su3_to8(D)[1]
+
+
+@pytest.mark.parametrize("anti", [False, True])
+def test_temporal_gauge_reading(rand_lattice, anti):
+    """The temporal-gauge transformation as read from Sec. 4.3:
+    G(x, 0) = 1, G(x, t+1) = G(x, t) U_4(x, t).  The transformed temporal
+    links are the unit matrix off the last time slice, the last slice holds
+    the product of U_4 around the time direction (gauge-invariant trace), and
+    the operator transforms covariantly, D[U'] G psi = G D[U] psi."""
+    dims, U, _, psi = rand_lattice
+    X, Y, Z, T = dims
+    ns = X * Y * Z
+    V = li.volume(dims)
+    U4 = U.reshape(T, ns, 4, 3, 3)[:, :, 3]
+    G = np.empty((T, ns, 3, 3), dtype=np.complex128)
+    G[0] = np.eye(3)
+    for t in range(1, T):
+        G[t] = G[t - 1] @ U4[t - 1]
+    G = G.reshape(V, 3, 3)
+    x, y, z, t = li.coords(dims)
+    Up = np.empty_like(U)
+    for mu in range(4):
+        c = [x, y, z, t]
+        c[mu] = (c[mu] + 1) % dims[mu]
+        fwd = li.lex_index(dims, *c)
+        Up[:, mu] = G @ U[:, mu] @ G[fwd].conj().transpose(0, 2, 1)
+    last = (t == T - 1)
+    assert np.abs(Up[~last, 3] - np.eye(3)).max() < 1e-13
+    # on the last slice: the ordered product U_4(x,0) ... U_4(x,T-1)
+    prod = np.broadcast_to(np.eye(3), (ns, 3, 3)).copy()
+    for tt in range(T):
+        prod = prod @ U4[tt]
+    assert np.abs(Up[last, 3] - prod).max() < 1e-12
+    psip = np.einsum("sij,saj->sai", G, psi)
+    got = oracle.dslash(psip, Up, dims, tbc_anti=anti)
+    want = np.einsum("sij,saj->sai", G, oracle.dslash(psi, U, dims, tbc_anti=anti))
+    assert np.abs(got - want).max() < 1e-12
