@@ -118,3 +118,62 @@ def test_codec_mutation_is_caught(name, tmp_path, monkeypatch):
         except AssertionError:
             caught += 1
     assert caught > 0, f"no pin caught the planted mistake: {name}"
+
+
+# Mistakes in the two functions that check the full-size GPU cases and give
+# the timed CPU baseline: the site-list operator and the fixed-count Schur
+# BiCGstab.  Each must fail one of the pins written for them.
+SAMPLE_MUTATIONS = {
+    "site list ignores the dagger flag": ("dslash_site(&L, p, dagger, sites[k], r);",
+                                          "dslash_site(&L, p, 0, sites[k], r);"),
+    "site list read in reverse order": ("dslash_site(&L, p, dagger, sites[k], r);",
+                                        "dslash_site(&L, p, dagger, sites[n - 1 - k], r);"),
+    "iterations on the odd part of the source": ("zero_parity(rhs, dims, 1);", "zero_parity(rhs, dims, 0);"),
+    "iterations on the full matrix instead of the Schur complement": ("tbc_anti, kappa, 1};",
+                                                                      "tbc_anti, kappa, 0};"),
+}
+SAMPLE_FUNCS = ("wo_dslash_sites", "wo_bicgstab_schur_iters")
+
+
+def _sample_checks():
+    return [
+        lambda: pins.test_dslash_sites_equals_full_lattice_dslash((4, 6, 8, 10), True, True),
+        lambda: pins.test_dslash_sites_free_field_closed_form((6, 4, 2, 12), False, False),
+        lambda: pins.test_bicgstab_schur_iterations_equal_truncated_solve((4, 6, 4, 8), 3),
+        pins.test_bicgstab_schur_iterations_free_field,
+    ]
+
+
+def test_unmutated_oracle_passes_sample_checks():
+    for chk in _sample_checks():
+        chk()
+
+
+@pytest.mark.parametrize("name", list(SAMPLE_MUTATIONS))
+def test_sample_mutation_is_caught(name, tmp_path, monkeypatch):
+    old, new = SAMPLE_MUTATIONS[name]
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old}"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    so = str(tmp_path / "mut.so")
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                           "-fcx-limited-range", "-o", so, str(path), "-lm"])
+    good = oracle._load()
+    mutated = ctypes.CDLL(so)
+    for fname in SAMPLE_FUNCS:
+        f, g = getattr(mutated, fname), getattr(good, fname)
+        f.argtypes, f.restype = g.argtypes, g.restype
+
+    class Shim:
+        def __getattr__(self, item):
+            return getattr(mutated, item) if item in SAMPLE_FUNCS else getattr(good, item)
+
+    monkeypatch.setattr(oracle, "_lib", Shim())
+    caught = 0
+    for chk in _sample_checks():
+        try:
+            chk()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, f"no pin caught the planted mistake: {name}"

@@ -420,3 +420,105 @@ def test_temporal_gauge_reading(rand_lattice, anti):
     got = oracle.dslash(psip, Up, dims, tbc_anti=anti)
     want = np.einsum("sij,saj->sai", G, oracle.dslash(psi, U, dims, tbc_anti=anti))
     assert np.abs(got - want).max() < 1e-12
+
+
+# ---- D at a list of sites (the checker of the full-size GPU parity tests)
+def _boundary_sites(dims, rng, n_random=200):
+    """Every combination of {0, 1, middle, L-2, L-1} per direction (all corner,
+    edge and face patterns of the boundary, both parities), random sites, and
+    duplicates in shuffled order."""
+    picks = [sorted({0, 1, d // 2, d - 2, d - 1}) for d in dims]
+    grid = np.stack(np.meshgrid(*picks, indexing="ij"), axis=-1).reshape(-1, 4)
+    lex = li.lex_index(dims, grid[:, 0], grid[:, 1], grid[:, 2], grid[:, 3])
+    rnd = rng.integers(0, li.volume(dims), size=n_random)
+    sites = np.concatenate([lex, rnd, lex[::7], rnd[:17]])
+    rng.shuffle(sites)
+    return sites.astype(np.int64)
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 8, 10), (6, 4, 2, 12)])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("anti", [False, True])
+def test_dslash_sites_equals_full_lattice_dslash(dims, dagger, anti):
+    """D psi at a list of sites equals the (pinned) full-lattice D psi at those
+    sites, bit for bit, for both parities, with duplicated and unordered
+    entries in the list."""
+    rng = np.random.default_rng(31)
+    U = li.gauge(dims, 0.5, 1011)
+    psi = li.gaussian_spinor(dims, 2011)
+    sites = _boundary_sites(dims, rng)
+    got = oracle.dslash_sites(psi, U, dims, sites, dagger=dagger, tbc_anti=anti)
+    full = oracle.dslash(psi, U, dims, dagger=dagger, tbc_anti=anti)
+    np.testing.assert_array_equal(got, full[sites])
+    par = li.parity(dims)[sites]
+    for p in (0, 1):
+        one = oracle.dslash(psi, U, dims, dagger=dagger, out_parity=p, tbc_anti=anti)
+        np.testing.assert_array_equal(got[par == p], one[sites[par == p]])
+    assert set(par.tolist()) == {0, 1}
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 8, 10), (6, 4, 2, 12)])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("anti", [False, True])
+def test_dslash_sites_free_field_closed_form(dims, dagger, anti):
+    """D psi at listed sites against the plane-wave closed form
+    D(p) = sum_mu (2 cos p_mu -+ 2 i gamma_mu sin p_mu), independently of the
+    full-lattice operator."""
+    rng = np.random.default_rng(32)
+    u = rng.normal(size=(4, 3)) + 1j * rng.normal(size=(4, 3))
+    psi, p = plane_wave(dims, (1, 1, 1, 2), u, anti)
+    sites = _boundary_sites(dims, rng)
+    got = oracle.dslash_sites(psi, li.unit_gauge(dims), dims, sites, dagger=dagger, tbc_anti=anti)
+    want = spin_apply(d_of_p(p, dagger), psi[sites])
+    assert np.abs(got - want).max() < 1e-12
+
+
+# ---- a fixed number of Schur BiCGstab iterations (the timed CPU baseline)
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (4, 6, 4, 8)])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_bicgstab_schur_iterations_equal_truncated_solve(dims, n):
+    """n iterations on the even part of b leave the residual |b_e - M_hat x_e|
+    that the (pinned) Schur solve reports after the same n iterations: with
+    b_o = 0, b_hat = b_e and the full residual equals the Schur residual."""
+    kappa = 0.124
+    U = li.gauge(dims, 0.5, 1012)
+    b = li.gaussian_spinor(dims, 2012) * (li.parity(dims) == 0)[:, None, None]
+    got = oracle.bicgstab_schur_iterations(b, U, dims, kappa, n)
+    _, st, iters, rel = oracle.solve(b, U, dims, kappa, tol=1e-300, maxiter=n, solver="bicgstab", schur=True)
+    assert st == 1 and iters == n
+    want = rel * np.linalg.norm(b)
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_bicgstab_schur_iterations_free_field():
+    """Closed form on the free field.  For an even plane wave, M_hat acts as the
+    4x4 spin matrix A = 1 - kappa^2 D(p)^2, which has exactly two distinct
+    eigenvalues (D(p)^2 = a^2 - |b|^2 - 2 i a (b.gamma), (b.gamma)^2 = |b|^2).
+    Two BiCGstab iterations contain two BiCG steps, which end with a zero
+    residual for such an operator.  After one iteration the residual is the
+    BiCG step's s = r - alpha A r, alpha = <r, r> / <r, A r>, minimised over
+    omega along A s."""
+    dims = (4, 6, 4, 8)
+    kappa = 0.124
+    rng = np.random.default_rng(33)
+    u = rng.normal(size=(4, 3)) + 1j * rng.normal(size=(4, 3))
+    psi, p = plane_wave(dims, (1, 1, 0, 3), u)
+    even = (li.parity(dims) == 0)[:, None, None]
+    b = psi * even
+    Dp = d_of_p(p)
+    A = np.eye(4) - kappa ** 2 * Dp @ Dp
+    assert len(set(np.round(np.linalg.eigvals(A), 10))) == 2
+    U = li.unit_gauge(dims)
+    bn = np.linalg.norm(b)
+    # one iteration: every even site carries the same spin-colour vector up to a phase
+    nsite = int(even.sum())
+    Au = A @ u
+    alpha = np.vdot(u, u) / np.vdot(u, Au)
+    s = u - alpha * Au
+    As = A @ s
+    omega = np.vdot(As, s) / np.vdot(As, As)
+    r1 = np.linalg.norm(s - omega * As) * np.sqrt(nsite)
+    got1 = oracle.bicgstab_schur_iterations(b, U, dims, kappa, 1)
+    assert abs(got1 - r1) <= 1e-12 * bn and r1 > 1e-3 * bn
+    got2 = oracle.bicgstab_schur_iterations(b, U, dims, kappa, 2)
+    assert got2 <= 1e-12 * bn
