@@ -349,10 +349,16 @@ const char *wd_server_last_error(const wd_server *server);
  *            parity (the scratch holds 65,536 partial sums of 256 sites);
  *            larger lattices are rejected with WD_ERR_INVALID_ARG.
  *   err    : optional buffer of err_len bytes for a one-line error message.
- * The first call on a device looks up the scratch address on that device;
- * make it before any stream capture.  All calls share the scratch: calls that
- * overlap on the GPU (other streams, other host threads) race and must not be
- * issued. */
+ * The first call in each CUDA context (the device's primary context for
+ * runtime-API callers; a driver-API caller's own context; a new primary
+ * context after cudaDeviceReset) looks up the scratch address in that context
+ * and caches it under the context's unique id; make that first call before
+ * any stream capture.  All calls share the scratch, whose counter is cleared
+ * on the stream before each launch: calls that overlap on the GPU (other
+ * streams, other host threads) race and must not be issued.
+ * Errors: WD_ERR_INVALID_ARG for null pointers, a bad precision, odd or too
+ * large dims (nothing is launched); WD_ERR_CUDA when no context can be made
+ * current or a launch fails. */
 wd_status wd_norm2_noalloc(double *result, const void *field, const int dims[4], wd_prec prec, void *cuda_stream,
                            char *err, size_t err_len);
 

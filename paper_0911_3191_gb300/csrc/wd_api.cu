@@ -666,6 +666,9 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   wd_status result = (wd_status)hc.status;
   if (result == WD_OK && !hc.done) result = WD_ERR_NOT_CONVERGED;
   if (!std::isfinite(r2)) result = WD_ERR_NUMERIC;
+  // the device stops on the Schur residual of its last reliable update; the
+  // full residual of the reconstructed x is the one reported, and it decides
+  if (result == WD_OK && r2 > p.tol * p.tol * b2) result = WD_ERR_NOT_CONVERGED;
   if (info) {
     info->iters = hc.iter + hc.updates;
     info->reliable_updates = hc.updates;
@@ -723,7 +726,10 @@ wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, c
 }
 
 // host lexicographic FP64 field -> both parities of a device FP64 field, one
-// host-to-device copy; stream-ordered, returns once the host array may be reused
+// host-to-device copy, stream-ordered.  For pageable host memory the copy has
+// read the array when this returns; for page-locked memory it is still in
+// flight, and the array may be reused only once the stream has reached this
+// point (an event or a synchronisation)
 wd_status wd_internal_import_full(wd_ctx* ctx, void* even, void* odd, const double* host) {
   Ctx& c = ctx->c;
   wd_status st = ensure_staging(ctx);

@@ -14,12 +14,19 @@
 // that scratch is a file-scope static __device__ array, so every GPU that
 // loads the library holds it (kScratchBytes, about 512 KB) until the process
 // exits.  Host code cannot use the array's name as a device address, so the
-// first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it; make that first call before any
-// stream capture.  Every call shares the array: the counter is cleared on the
-// stream before each launch, and calls that overlap on the GPU (different
-// streams, or different host threads at once) race on it.
+// first call in each CUDA context looks the address up with
+// cudaGetSymbolAddress (with that context current) and caches it under the
+// context's unique id; make that first call before any stream capture.  The
+// address belongs to the context, not to the device: a driver-API caller with
+// its own context, or a caller that reset the device (which ends the primary
+// context), gets a fresh lookup in the new context.  Every call shares the
+// array: the counter is cleared on the stream before each launch, and calls
+// that overlap on the GPU (different streams, or different host threads at
+// once) race on it.
+#include <cuda.h>
+
 #include <mutex>
+#include <unordered_map>
 
 #include "wd_kernels.cuh"
 
@@ -30,12 +37,11 @@ constexpr int kNoallocBlock = 256;
 constexpr int kMaxPartials = 65536;  // one per block: Vh <= 65536 * 256 = 16,777,216 sites
 constexpr size_t kCounterOffset = (size_t)kMaxPartials * sizeof(double);
 constexpr size_t kScratchBytes = kCounterOffset + 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+std::unordered_map<unsigned long long, void*> g_scratch_addr;  // context id -> address
 
 void put_err(char* err, size_t len, const char* msg) {
   if (!err || len == 0) return;
@@ -44,16 +50,54 @@ void put_err(char* err, size_t len, const char* msg) {
   err[i] = 0;
 }
 
-// Once per device, with that device current: the device address of the array.
-cudaError_t scratch_address(int device, void** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = p;
+// The current context's unique id, through the driver entry points that the
+// runtime hands out (no link against the driver library).  0 when no context
+// is current yet.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorNotSupported;
+    get_current = (CtxGetCurrentFn)f1;
+    get_id = (CtxGetIdFn)f2;
   }
-  *out = g_scratch_addr[device];
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Once per context, with that context current: the device address of the
+// array.  The runtime binds the device's primary context on its first call
+// when none is current, so the id is read again after the lookup.
+cudaError_t scratch_address(void** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  unsigned long long id = 0;
+  cudaError_t e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  if (id) {
+    auto it = g_scratch_addr.find(id);
+    if (it != g_scratch_addr.end()) {
+      *out = it->second;
+      return cudaSuccess;
+    }
+  }
+  void* p = nullptr;
+  if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+  if ((e = current_context_id(&id)) != cudaSuccess) return e;
+  if (!id) return cudaErrorDeviceUninitialized;
+  g_scratch_addr[id] = p;
+  *out = p;
   return cudaSuccess;
 }
 
@@ -93,15 +137,11 @@ extern "C" wd_status wd_norm2_noalloc(double* result, const void* field, const i
     return WD_ERR_INVALID_ARG;
   }
   const Geom g = make_geom(dims, 0);
-  int device = 0;
-  cudaError_t e = cudaGetDevice(&device);
-  if (e != cudaSuccess || device < 0 || device >= kMaxDevices) {
-    put_err(err, err_len, "wd_norm2_noalloc: no usable current device");
-    return WD_ERR_CUDA;
-  }
   void* scratch = nullptr;
-  if ((e = scratch_address(device, &scratch)) != cudaSuccess) {
-    put_err(err, err_len, "wd_norm2_noalloc: cudaGetSymbolAddress of the static scratch failed");
+  cudaError_t e = scratch_address(&scratch);
+  if (e != cudaSuccess) {
+    put_err(err, err_len, "wd_norm2_noalloc: no usable current context, or cudaGetSymbolAddress of the static "
+                          "scratch failed");
     return WD_ERR_CUDA;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -414,6 +414,8 @@ wd_status finish(wd_server* sv, Request& q) {
   wd_status rs = (wd_status)hc.status;
   if (rs == WD_OK && !hc.done) rs = WD_ERR_NOT_CONVERGED;
   if (b2 > 0.0 && !std::isfinite(r2)) rs = WD_ERR_NUMERIC;
+  // the reported full residual of the reconstructed x decides convergence
+  if (rs == WD_OK && b2 > 0.0 && r2 > q.tol * q.tol * b2) rs = WD_ERR_NOT_CONVERGED;
   q.info.iters = hc.iter + hc.updates;
   q.info.reliable_updates = hc.updates;
   q.info.true_rel_residual = b2 > 0.0 ? std::sqrt(r2 / b2) : 0.0;

@@ -131,7 +131,10 @@ wd_status ensure_batch(wd_ctx* ctx, int n, int prec) {
 
 std::string tune_key(const Ctx& c, int n, int prec) {
   std::ostringstream k;
-  k << c.g.X << "x" << c.g.Y << "x" << c.g.Z << "x" << c.g.T << " prec" << prec << " n" << n << " sms" << c.num_sms;
+  // the link format and the temporal gauge change the cost of the multi-RHS
+  // dslash, so a shape tuned for one is not reused for the other
+  k << c.g.X << "x" << c.g.Y << "x" << c.g.Z << "x" << c.g.T << " prec" << prec << " n" << n << " sms" << c.num_sms
+    << " links" << c.low_recon << " tfix" << c.g.tfix;
   return k.str();
 }
 
@@ -331,6 +334,8 @@ wd_status solve_batch_device(wd_ctx* ctx, int n, void* x, const void* bsrc, cons
     wd_status sr = (wd_status)hc[r].status;
     if (sr == WD_OK && !hc[r].done) sr = WD_ERR_NOT_CONVERGED;
     if (b2 > 0.0 && !std::isfinite(r2)) sr = WD_ERR_NUMERIC;
+    // the reported full residual of the reconstructed x decides convergence
+    if (sr == WD_OK && b2 > 0.0 && r2 > p.tol * p.tol * b2) sr = WD_ERR_NOT_CONVERGED;
     if (infos) {
       infos[r].iters = hc[r].iter + hc[r].updates;
       infos[r].reliable_updates = hc[r].updates;

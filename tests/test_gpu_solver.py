@@ -194,3 +194,20 @@ def test_xhat_in_fp32(small, solver, prec):
     r2 = wd.solve(x2, b, kappa, tol=1e-12, solver=solver, inner_precision=prec, xhat_f32=True, use_graph=False)
     assert (r.iters, r.reliable_updates) == (r2.iters, r2.reliable_updates)
     np.testing.assert_array_equal(x, x2)
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("prec", [0, 2, 4])
+def test_status_ok_implies_reported_residual_below_tol(small, solver, prec):
+    """A solve that returns WD_OK reports a full FP64 true residual at or below
+    tol, and the oracle agrees; any solve whose reconstructed x misses tol
+    returns WD_ERR_NOT_CONVERGED instead."""
+    m, wd, dims, kappa, U, b, _, _ = small
+    for tol in (1e-5, 1e-7, 1e-9, 1e-11):
+        x = np.zeros_like(b)
+        r = wd.solve(x, b, kappa, tol=tol, delta=0.1, solver=solver, inner_precision=prec, check=False)
+        rel = oracle.true_residual(x, b, U, dims, kappa)
+        if r.status == 0:
+            assert r.true_rel_residual <= tol and rel <= tol * (1 + 1e-6), (tol, r, rel)
+        else:
+            assert r.status == 4 and r.true_rel_residual > tol, (tol, r)
