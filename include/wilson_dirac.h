@@ -149,6 +149,53 @@ wd_status wd_dslash(wd_ctx *ctx, void *out, const void *in, wd_parity out_parity
 wd_status wd_dslash_xpay(wd_ctx *ctx, void *out, const void *in, const void *x, double a, wd_parity out_parity,
                          int dagger, wd_prec prec);
 
+/* ---- T-slab domain decomposition (Sec. 6 names multi-GPU operation as the
+ * next step).  A context created with dims {X, Y, Z, nt} holds one slab of a
+ * lattice {X, Y, Z, T}: the nt time slices t0 .. t0 + nt - 1 of one rank, nt
+ * even and t0 even, so local and global site parities agree.  Its links are
+ * the slab's own (wd_load_gauge with the slab's sites; general links: no
+ * temporal gauge, 12-real FP32 / 16-bit copies).  A dslash on the slab needs
+ * from each time neighbour one boundary slice of the input spinor, projected
+ * by the temporal hop's projector (1 -+ gamma_4): in the internal basis this
+ * is a half spinor, 12 reals per site, the same half the temporal hop of the
+ * stencil reads.  The first slice's backward hop also needs U_4 on the lower
+ * neighbour's last slice (the "link face", once per gauge field).
+ * The caller moves the faces between ranks (the Python binding uses
+ * torch.distributed point-to-point messages: NCCL on GPUs, gloo on CPUs; with
+ * one rank the halos are the rank's own opposite faces) into buffers in the
+ * receiving GPU's own memory, and passes them to wd_dslash_slab.
+ *
+ * Face buffers are device buffers of wd_slab_face_bytes / wd_slab_link_face_bytes
+ * bytes, owned by the caller.  Both sizes depend on the context's dims and,
+ * for the link face, on its FP64 link storage (12 or 18 reals). */
+size_t wd_slab_face_bytes(const wd_ctx *ctx, wd_prec prec);
+size_t wd_slab_link_face_bytes(const wd_ctx *ctx, wd_prec prec);
+
+/* Project the boundary slices of the single-parity input field `in` (the
+ * field a following wd_dslash_slab reads):
+ *   face_lo <- slice 0, for the lower neighbour's forward temporal hop,
+ *   face_hi <- slice nt-1, for the upper neighbour's backward temporal hop,
+ * each the half spinor that hop projects onto for D (dagger = 0) or D^dag.
+ * Stored words are copied unchanged (16-bit codes keep their site norm). */
+wd_status wd_slab_pack_faces(wd_ctx *ctx, void *face_lo, void *face_hi, const void *in, int dagger, wd_prec prec);
+
+/* U_4 of the slab's last slice, both parities, in the precision-prec link
+ * copy's own words, for the upper neighbour's link halo. */
+wd_status wd_slab_pack_link_face(wd_ctx *ctx, void *link_face, wd_prec prec);
+
+/* out = D_{p,1-p} in on the slab (dagger: D^dag), p = out_parity, for the
+ * output sites of `region`: 0 = interior slices 1 .. nt-2 (needs no halo, so
+ * it can run while the faces travel), 1 = the two boundary slices, 2 = all.
+ * halo_lo: the lower neighbour's face_hi; halo_hi: the upper neighbour's
+ * face_lo; link_halo: the lower neighbour's link face (all three may be NULL
+ * for region 0).  flip_lo / flip_hi: nonzero when that halo crosses the
+ * global t = T-1 <-> 0 boundary of an antiperiodic time direction (a factor
+ * -1).  Errors: WD_ERR_INVALID_ARG for bad pointers, an odd or too small nt,
+ * the temporal gauge or 8-number links. */
+wd_status wd_dslash_slab(wd_ctx *ctx, void *out, const void *in, const void *halo_lo, const void *halo_hi,
+                         const void *link_halo, int flip_lo, int flip_hi, wd_parity out_parity, int dagger,
+                         wd_prec prec, int region);
+
 /* Apply the Wilson-Dirac matrix (Sec. 3).  WD_M_FULL: out = M_kappa in on full
  * fields (even then odd).  WD_M_SCHUR_EVEN: out = M_hat in on even fields
  * (Sec. 3 Schur complement); the odd temporary is context workspace.

@@ -120,6 +120,11 @@ def load_library():
         "wd_server_memory_in_use": (ctypes.c_size_t, [vp]),
         "wd_server_get_stats": (c_int, [vp, ctypes.POINTER(ServerStats)]),
         "wd_server_last_error": (ctypes.c_char_p, [vp]),
+        "wd_slab_face_bytes": (ctypes.c_size_t, [vp, c_int]),
+        "wd_slab_link_face_bytes": (ctypes.c_size_t, [vp, c_int]),
+        "wd_slab_pack_faces": (c_int, [vp, vp, vp, vp, c_int, c_int]),
+        "wd_slab_pack_link_face": (c_int, [vp, vp, c_int]),
+        "wd_dslash_slab": (c_int, [vp, vp, vp, vp, vp, vp, c_int, c_int, c_int, c_int, c_int, c_int]),
         "wd_last_error": (ctypes.c_char_p, [vp]),
         "wd_status_string": (ctypes.c_char_p, [c_int]),
     }
@@ -140,6 +145,8 @@ def exported_symbols():
                         "wd_solve_multishift", "wd_solve_multishift_device", "wd_server_create", "wd_server_destroy", "wd_server_add_gauge", "wd_server_submit",
                         "wd_server_step", "wd_server_poll", "wd_server_memory_in_use", "wd_server_last_error",
                         "wd_server_get_stats",
+                        "wd_slab_face_bytes", "wd_slab_link_face_bytes", "wd_slab_pack_faces",
+                        "wd_slab_pack_link_face", "wd_dslash_slab",
                         "wd_norm2_noalloc", "wd_last_error", "wd_status_string")
             if hasattr(lib, n)]
 
@@ -241,6 +248,28 @@ class WilsonDirac:
     def dslash_xpay(self, out, inp, x, a: float, out_parity: int, dagger: bool, prec: int):
         self._check(self.lib.wd_dslash_xpay(self.ctx, _ptr(out), _ptr(inp), _ptr(x), float(a), out_parity,
                                             int(dagger), prec), "dslash_xpay")
+
+    # -- T-slab decomposition (one rank's slab; see tslab.SlabDslash)
+    def slab_face_bytes(self, prec: int) -> int:
+        return int(self.lib.wd_slab_face_bytes(self.ctx, prec))
+
+    def slab_link_face_bytes(self, prec: int) -> int:
+        return int(self.lib.wd_slab_link_face_bytes(self.ctx, prec))
+
+    def slab_pack_faces(self, face_lo, face_hi, inp, dagger: bool, prec: int):
+        self._check(self.lib.wd_slab_pack_faces(self.ctx, _ptr(face_lo), _ptr(face_hi), _ptr(inp), int(dagger), prec),
+                    "slab_pack_faces")
+
+    def slab_pack_link_face(self, face, prec: int):
+        self._check(self.lib.wd_slab_pack_link_face(self.ctx, _ptr(face), prec), "slab_pack_link_face")
+
+    def dslash_slab(self, out, inp, halo_lo, halo_hi, link_halo, flip_lo: bool, flip_hi: bool, out_parity: int,
+                    dagger: bool, prec: int, region: int):
+        """region 0: interior slices, 1: the two boundary slices, 2: all."""
+        p = [None if a is None else ctypes.c_void_p(_ptr(a)) for a in (halo_lo, halo_hi, link_halo)]
+        self._check(self.lib.wd_dslash_slab(self.ctx, _ptr(out), _ptr(inp), p[0], p[1], p[2], int(bool(flip_lo)),
+                                            int(bool(flip_hi)), out_parity, int(dagger), prec, int(region)),
+                    "dslash_slab")
 
     def apply_M(self, out, inp, kappa: float, which: int, dagger: bool, prec: int):
         self._check(self.lib.wd_apply_M(self.ctx, _ptr(out), _ptr(inp), float(kappa), which, int(dagger), prec),

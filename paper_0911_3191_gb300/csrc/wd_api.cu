@@ -646,17 +646,18 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   // x_e from the accumulator, x_o = b_o + kappa D_oe x_e (Sec. 3: the full
   // solution is reconstructed from the Schur solution)
   WD_CK(ctx, cudaMemcpyAsync(x_e, sb.x, f64, cudaMemcpyDeviceToDevice, s));
-  o64->dslash_xpay(c, x_o, x_e, b_o, kappa, nullptr, 1, 0, s);
-  // S13: full FP64 true residual |b - M x|
+  // S13: full FP64 true residual |b - M x|.  The odd rows come with x_o
+  // itself: one FP64 D_oe x_e gives x_o = b_o + kappa D_oe x_e and
+  // r_o = b_o - (x_o - kappa D_oe x_e); the even rows need D_eo x_o.
   {
     using T64 = Tr<WD_F64>;
+    EpiReconResid<FinStore> eo{T64::view(x_o, c.g), T64::view(b_o, c.g), Coef{kappa, nullptr}, c.red,
+                               FinStore{c.scalars + 5, 1}};
+    launch_dslash<double>(c, T64::view(x_e, c.g), T64::gauge(c), 1, 0, eo, s);
     const Coef ck{-kappa, nullptr};
     EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> ee{T64::view(nullptr, c.g), false, T64::view(b_e, c.g),
                                                            T64::view(x_e, c.g), ck, c.red, FinStore{c.scalars + 4, 1}};
     launch_dslash<double>(c, T64::view(x_o, c.g), T64::gauge(c), 0, 0, ee, s);
-    EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> eo{T64::view(nullptr, c.g), false, T64::view(b_o, c.g),
-                                                           T64::view(x_o, c.g), ck, c.red, FinStore{c.scalars + 5, 1}};
-    launch_dslash<double>(c, T64::view(x_e, c.g), T64::gauge(c), 1, 0, eo, s);
   }
   WD_CK_LAUNCH(ctx, "reconstruction");
   WD_CK(ctx, cudaMemcpyAsync(&hc, sb.ctl, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -678,11 +679,12 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     // setup: 3 norms, b_hat, zero x, control init, solver setup (4 kernels,
     // CG: 2 dslash + 2 zero); per iteration: BiCGstab 7 (CG 5) + loop control;
-    // per reliable update: BiCGstab 3 (CG 5); end: x_o and two residual dslash
+    // per reliable update: BiCGstab 3 (CG 5); end: x_o with the odd residual,
+    // and the even residual dslash
     const long long setup = 3 + 1 + 1 + 1 + 4;
     const long long per_it = (p.solver == WD_BICGSTAB ? 7 : 5) + (p.use_graph ? 1 : 0);
     const long long per_up = (p.solver == WD_BICGSTAB) ? 4 : 5;
-    info->kernel_launches = setup + (long long)hc.iter * per_it + (long long)hc.updates * per_up + 3;
+    info->kernel_launches = setup + (long long)hc.iter * per_it + (long long)hc.updates * per_up + 2;
   }
   if (result != WD_OK) {
     char m[160];
@@ -962,6 +964,70 @@ wd_status wd_dslash(wd_ctx* ctx, void* out, const void* in, wd_parity out_parity
   if (st != WD_OK) return st;
   prec_ops(prec)->dslash(ctx->c, out, in, out_parity, dagger ? 1 : 0, ctx->c.stream);
   WD_CK_LAUNCH(ctx, "wd_dslash");
+  return WD_OK;
+}
+
+// ---- T-slab decomposition (Sec. 6)
+static wd_status slab_check(wd_ctx* ctx, int prec, const char* what) {
+  if (!ctx || !valid_prec(prec)) return set_err(ctx, WD_ERR_INVALID_ARG, std::string(what) + ": bad args");
+  Ctx& c = ctx->c;
+  if (c.g.T < 2 || (c.g.T & 1))
+    return set_err(ctx, WD_ERR_INVALID_ARG, std::string(what) + ": the slab's T must be even and >= 2");
+  if (c.gauge_loaded && (c.g.tfix || (prec != WD_F64 && c.low_recon != 12)))
+    return set_err(ctx, WD_ERR_INVALID_ARG,
+                   std::string(what) + ": slabs take general links with 12-real FP32 / 16-bit copies (no temporal "
+                                       "gauge, no 8-number links)");
+  return WD_OK;
+}
+
+size_t wd_slab_face_bytes(const wd_ctx* ctx, wd_prec prec) {
+  if (!ctx || !valid_prec(prec)) return 0;
+  return prec_ops(prec)->slab_face_bytes(ctx->c);
+}
+
+size_t wd_slab_link_face_bytes(const wd_ctx* ctx, wd_prec prec) {
+  if (!ctx || !valid_prec(prec)) return 0;
+  return prec_ops(prec)->slab_link_face_bytes(ctx->c);
+}
+
+wd_status wd_slab_pack_faces(wd_ctx* ctx, void* face_lo, void* face_hi, const void* in, int dagger, wd_prec prec) {
+  wd_status st = slab_check(ctx, prec, "wd_slab_pack_faces");
+  if (st != WD_OK) return st;
+  if (!face_lo || !face_hi || !in || face_lo == face_hi)
+    return set_err(ctx, WD_ERR_INVALID_ARG, "wd_slab_pack_faces: bad pointers");
+  WD_CK(ctx, cudaSetDevice(ctx->c.device));
+  prec_ops(prec)->slab_pack_faces(ctx->c, face_lo, face_hi, in, dagger ? 1 : 0, ctx->c.stream);
+  WD_CK_LAUNCH(ctx, "wd_slab_pack_faces");
+  return WD_OK;
+}
+
+wd_status wd_slab_pack_link_face(wd_ctx* ctx, void* link_face, wd_prec prec) {
+  wd_status st = slab_check(ctx, prec, "wd_slab_pack_link_face");
+  if (st != WD_OK) return st;
+  if (!link_face) return set_err(ctx, WD_ERR_INVALID_ARG, "wd_slab_pack_link_face: null face");
+  WD_CK(ctx, cudaSetDevice(ctx->c.device));
+  if ((st = ensure_gauge(ctx, prec)) != WD_OK) return st;
+  if ((st = slab_check(ctx, prec, "wd_slab_pack_link_face")) != WD_OK) return st;
+  prec_ops(prec)->slab_pack_link_face(ctx->c, link_face, ctx->c.stream);
+  WD_CK_LAUNCH(ctx, "wd_slab_pack_link_face");
+  return WD_OK;
+}
+
+wd_status wd_dslash_slab(wd_ctx* ctx, void* out, const void* in, const void* halo_lo, const void* halo_hi,
+                         const void* link_halo, int flip_lo, int flip_hi, wd_parity out_parity, int dagger,
+                         wd_prec prec, int region) {
+  wd_status st = slab_check(ctx, prec, "wd_dslash_slab");
+  if (st != WD_OK) return st;
+  if (!out || !in || out == in || (out_parity != 0 && out_parity != 1) || region < 0 || region > 2)
+    return set_err(ctx, WD_ERR_INVALID_ARG, "wd_dslash_slab: bad args");
+  if (region != 0 && (!halo_lo || !halo_hi || !link_halo))
+    return set_err(ctx, WD_ERR_INVALID_ARG, "wd_dslash_slab: the boundary slices need both halos and the link halo");
+  WD_CK(ctx, cudaSetDevice(ctx->c.device));
+  if ((st = ensure_gauge(ctx, prec)) != WD_OK) return st;
+  if ((st = slab_check(ctx, prec, "wd_dslash_slab")) != WD_OK) return st;
+  prec_ops(prec)->slab_dslash(ctx->c, out, in, halo_lo, halo_hi, link_halo, flip_lo ? 1 : 0, flip_hi ? 1 : 0,
+                              out_parity, dagger ? 1 : 0, region, ctx->c.stream);
+  WD_CK_LAUNCH(ctx, "wd_dslash_slab");
   return WD_OK;
 }
 

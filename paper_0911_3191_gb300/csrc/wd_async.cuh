@@ -1,0 +1,190 @@
+// The dslash of one site for 16-bit storage (Sec. 4.6) with its neighbour
+// data staged through shared memory by asynchronous copies (cp.async).
+//
+// Each thread owns three stages of shared-memory slots (structure of arrays
+// by thread, so a warp's accesses are conflict-free).  A stage holds one
+// neighbour's stored words (a spinor: 3 x 16 B of codes and the 4 B norm; a
+// temporal half spinor: 24 B and the norm) and the link of the hop (16 B +
+// 8 B).  While hop k is computed the copies for hops k+1 and k+2 are in
+// flight, so the loads of eight hops overlap with the arithmetic without
+// holding any register; the arithmetic is that of hop() and hop_t() (the
+// same decoders, projections, SU(3) products and reconstructions, in the
+// same order).  Copies are ordered per thread: no thread reads another's
+// slots, so no barrier is needed.
+#pragma once
+
+#include "wd_device.cuh"
+
+namespace wd {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16_ca(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp16_cg(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp8_ca(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp4_ca(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kAsyncBlock = 128;  // threads per block of the kernels that use these slots
+constexpr int kAsyncStages = 3;
+
+struct AsyncSlots {
+  uint4 sp[kAsyncStages][3][kAsyncBlock];  // spinor words (temporal: 24 B in chunks 0, 1)
+  float sn[kAsyncStages][kAsyncBlock];     // site norm
+  uint4 l4[kAsyncStages][kAsyncBlock];     // link words 0..3
+  uint2 l2[kAsyncStages][kAsyncBlock];     // link words 4, 5
+};
+
+// hops in the order of dslash_site: x+, x-, y+, y-, z+, z-, t+, t-
+template <int K>
+struct HopK {
+  static constexpr int MU = K / 2;
+  static constexpr bool FWD = (K % 2) == 0;
+  static constexpr int ST = K % kAsyncStages;
+};
+
+template <int K, bool DAGGER, bool TFIX, class In, class G>
+__device__ __forceinline__ void async_issue(AsyncSlots& sm, const In& in, const G& gauge, int parity, int h,
+                                            const int (&nb)[8], bool top, bool bot) {
+  using H = HopK<K>;
+  const int tid = threadIdx.x;
+  const int n = nb[K];
+  const size_t st = (size_t)in.stride;
+  if constexpr (H::MU < 3) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cp16_ca(&sm.sp[H::ST][c][tid], in.p + c * st + n);
+  } else {
+    constexpr int S = (H::FWD != DAGGER) ? -1 : +1;
+    if constexpr (S == +1) {  // spins 0, 1: chunk 0 and the first half of chunk 1
+      cp16_ca(&sm.sp[H::ST][0][tid], in.p + n);
+      cp8_ca(&sm.sp[H::ST][1][tid], reinterpret_cast<const uint2*>(in.p + st + n));
+    } else {  // spins 2, 3: the second half of chunk 1 and chunk 2
+      cp8_ca(&sm.sp[H::ST][0][tid], reinterpret_cast<const uint2*>(in.p + st + n) + 1);
+      cp16_ca(&sm.sp[H::ST][1][tid], in.p + 2 * st + n);
+    }
+  }
+  cp4_ca(&sm.sn[H::ST][tid], in.norm + n);
+  // the temporal links of the temporal gauge are 1 off the last slice
+  const bool unit = TFIX && H::MU == 3 && (H::FWD ? !top : !bot);
+  if (!unit) {
+    const int slot = (H::FWD ? parity : 1 - parity) * 4 + H::MU;
+    const size_t o = (size_t)slot * gauge.stride + (H::FWD ? h : n);
+    cp16_cg(&sm.l4[H::ST][tid], gauge.p8 + o);
+    cp8_ca(&sm.l2[H::ST][tid], gauge.p4 + o);
+  }
+}
+
+template <int K, bool DAGGER, bool TFIX, class In, class G>
+__device__ __forceinline__ void async_hop(const AsyncSlots& sm, const Geom& g, bool top, bool bot, float (&acc)[24]) {
+  using H = HopK<K>;
+  constexpr int MU = H::MU;
+  constexpr bool FWD = H::FWD;
+  constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  const int tid = threadIdx.x;
+  float w = In::scale_of(sm.sn[H::ST][tid]);
+  const bool unit = TFIX && MU == 3 && (FWD ? !top : !bot);
+  float u[18];
+  if (!unit) {
+    const uint4 a = sm.l4[H::ST][tid];
+    const uint2 b = sm.l2[H::ST][tid];
+    const uint32_t lw[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    G::from_words(lw, u);
+    if constexpr (G::kScaled) w *= G::kScale;  // Q16 links come back as raw codes
+  }
+  if constexpr (MU < 3) {
+    uint32_t sw[12];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint4 d = sm.sp[H::ST][c][tid];
+      sw[4 * c] = d.x; sw[4 * c + 1] = d.y; sw[4 * c + 2] = d.z; sw[4 * c + 3] = d.w;
+    }
+    float psi[24], hs[12];
+    In::words_biased(sw, psi);
+    if constexpr (In::kBias != 0.f) project_biased<MU, S>(psi, hs, In::kBias);
+    else project<MU, S>(psi, hs);
+    float gs[12];
+    su3_mul<!FWD>(u, hs, gs);
+    reconstruct_scaled<MU, S>(gs, acc, w);
+  } else {
+    constexpr bool upper = (S == +1);
+    uint32_t hw[6];
+    if constexpr (upper) {
+      const uint4 a = sm.sp[H::ST][0][tid];
+      const uint2 b = *reinterpret_cast<const uint2*>(&sm.sp[H::ST][1][tid]);
+      hw[0] = a.x; hw[1] = a.y; hw[2] = a.z; hw[3] = a.w; hw[4] = b.x; hw[5] = b.y;
+    } else {
+      const uint2 a = *reinterpret_cast<const uint2*>(&sm.sp[H::ST][0][tid]);
+      const uint4 b = sm.sp[H::ST][1][tid];
+      hw[0] = a.x; hw[1] = a.y; hw[2] = b.x; hw[3] = b.y; hw[4] = b.z; hw[5] = b.w;
+    }
+    float hs[12];
+    In::words_half(hw, hs);
+    const bool flip = g.tbc_anti && (FWD ? top : bot);
+    if (unit) {
+      accumulate_temporal<FWD, upper>(hs, acc, flip ? -2.f * w : 2.f * w);
+    } else {
+      float gs[12];
+      su3_mul<!FWD>(u, hs, gs);
+      accumulate_temporal<FWD, upper>(gs, acc, flip ? -2.f * w : 2.f * w);
+    }
+  }
+}
+
+template <int K, bool DAGGER, bool TFIX, class In, class G>
+__device__ __forceinline__ void async_step(AsyncSlots& sm, const Geom& g, const In& in, const G& gauge, int parity,
+                                           int h, const int (&nb)[8], bool top, bool bot, float (&acc)[24]) {
+  if constexpr (K + 2 < 8) async_issue<K + 2, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
+  cp_commit();
+  cp_wait<2>();  // the copies of hop K have landed
+  async_hop<K, DAGGER, TFIX, In, G>(sm, g, top, bot, acc);
+}
+
+// acc = (D in)(h) (or D^dag), 16-bit spinors and 12-real 16-bit links; the
+// caller's block has kAsyncBlock threads.
+template <bool DAGGER, bool TFIX, class In, class G>
+__device__ __forceinline__ void dslash_site_async(const Geom& g, const In& in, const G& gauge, int h, int parity,
+                                                  float (&acc)[24]) {
+  __shared__ AsyncSlots sm;
+  int x, y, z, t;
+  site_coords(g, h, parity, x, y, z, t);
+  int nb[8];
+  {
+    const int xo = x & 1;
+    nb[0] = (x == g.X - 1) ? h - (g.Xh - 1) : h + xo;
+    nb[1] = (x == 0) ? h + (g.Xh - 1) : h - (xo ^ 1);
+    nb[2] = (y == g.Y - 1) ? h - g.wy : h + g.Xh;
+    nb[3] = (y == 0) ? h + g.wy : h - g.Xh;
+    nb[4] = (z == g.Z - 1) ? h - g.wz : h + g.XhY;
+    nb[5] = (z == 0) ? h + g.wz : h - g.XhY;
+    nb[6] = (t == g.T - 1) ? h - g.wt : h + g.XhYZ;
+    nb[7] = (t == 0) ? h + g.wt : h - g.XhYZ;
+  }
+  const bool top = (t == g.T - 1), bot = (t == 0);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] = 0.f;
+  async_issue<0, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
+  cp_commit();
+  async_issue<1, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
+  cp_commit();
+  async_step<0, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<1, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<2, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<3, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<4, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<5, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<6, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+  async_step<7, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
+}
+
+}  // namespace wd

@@ -263,22 +263,39 @@ struct Spinor16 {
       return pair(w);
     }
   }
-  // load_raw() with Q16 codes left as q + kBias (see project_biased)
-  __device__ __forceinline__ float load_raw_biased(int h, float (&v)[24]) const {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      uint4 d = __ldg(p + (size_t)c * stride + h);
-      const uint32_t w[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 f = pair_biased(w[j]);
-        v[8 * c + 2 * j] = f.x;
-        v[8 * c + 2 * j + 1] = f.y;
-      }
-    }
-    float n = __ldg(norm + h);
+  // the factor that turns raw values into field values, from the site norm
+  static __device__ __forceinline__ float scale_of(float n) {
     if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
     else return n;
+  }
+  // 24 raw values from the 12 stored words, Q16 codes as q + kBias
+  static __device__ __forceinline__ void words_biased(const uint32_t (&w)[12], float (&v)[24]) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const float2 f = pair_biased(w[j]);
+      v[2 * j] = f.x;
+      v[2 * j + 1] = f.y;
+    }
+  }
+  // 12 raw values of half a spinor from its 6 words
+  static __device__ __forceinline__ void words_half(const uint32_t (&w)[6], float (&v)[12]) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const float2 f = pair(w[j]);
+      v[2 * j] = f.x;
+      v[2 * j + 1] = f.y;
+    }
+  }
+  // load_raw() with Q16 codes left as q + kBias (see project_biased)
+  __device__ __forceinline__ float load_raw_biased(int h, float (&v)[24]) const {
+    uint32_t w[12];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint4 d = __ldg(p + (size_t)c * stride + h);
+      w[4 * c] = d.x; w[4 * c + 1] = d.y; w[4 * c + 2] = d.z; w[4 * c + 3] = d.w;
+    }
+    words_biased(w, v);
+    return scale_of(__ldg(norm + h));
   }
   // raw 16-bit values as float (codes, or the normalised fp16/bf16 numbers)
   // plus the factor that turns them into field values
@@ -311,15 +328,8 @@ struct Spinor16 {
       const uint4 b = __ldg(p + (size_t)2 * stride + h);
       w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = b.z; w[5] = b.w;
     }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const float2 f = pair(w[j]);
-      v[2 * j] = f.x;
-      v[2 * j + 1] = f.y;
-    }
-    float n = __ldg(norm + h);
-    if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
-    else return n;
+    words_half(w, v);
+    return scale_of(__ldg(norm + h));
   }
   template <typename R>
   __device__ __forceinline__ void load(int h, R (&v)[24]) const {
@@ -357,6 +367,27 @@ struct Spinor16 {
     float scale;
     if constexpr (F == Fmt16::Q16) scale = (m > 0.f) ? __fdiv_rn(32767.f, m) : 0.f;
     else scale = (m > 0.f) ? __fdiv_rn(1.f, m) : 0.f;
+    if constexpr (F == Fmt16::Q16) {
+      // q = rint(f * scale) without a conversion instruction: s = fl(f * scale)
+      // + 1.5 * 2^23 rounds to the nearest integer, ties to even, because
+      // |fl(f * scale)| <= 32767 (1 + 2^-24)^2 < 2^22 (so no clamp is needed
+      // either: m is the largest |f|); the low 16 bits of s are then q in two's
+      // complement, and s - 1.5 * 2^23 = q exactly
+      constexpr float kMagic = 12582912.0f;
+      float sv[24];
+#pragma unroll
+      for (int k = 0; k < 24; ++k) sv[k] = __fadd_rn(__fmul_rn(f[k], scale), kMagic);
+      uint32_t w[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) w[k] = __byte_perm(__float_as_uint(sv[2 * k]), __float_as_uint(sv[2 * k + 1]), 0x5410);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) p[(size_t)c * stride + h] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+      norm[h] = m;
+      const float d = __fmul_rn(m, kInv32767);
+#pragma unroll
+      for (int k = 0; k < 24; ++k) v[k] = (R)__fmul_rn(__fsub_rn(sv[k], kMagic), d);
+      return;
+    }
     uint32_t w[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) w[k] = enc(f[2 * k], scale) | (enc(f[2 * k + 1], scale) << 16);
@@ -384,6 +415,12 @@ using SpinorH16 = Spinor16<Fmt16::H16>;
 using SpinorB16 = Spinor16<Fmt16::B16>;
 
 // ------------------------------------------------------------- gauge fields
+// Link words are read once per dslash: streaming loads (evict first).
+template <class T>
+__device__ __forceinline__ T ld_link(const T* p) {
+  return __ldcs(p);
+}
+
 // Link U_mu(x), x of parity p with even-odd index h.  Reals index
 // k = (row * 3 + col) * 2 + reim.  12-real storage keeps rows a, b; the third
 // row is rebuilt as c = (a x b)^* (App. A.1).  Layout [p][mu][chunk][stride].
@@ -500,23 +537,32 @@ struct GaugeF64 {
   int stride;
   int recon;  // 12 or 18
   template <bool R8, typename R>
-  __device__ __forceinline__ void load_scaled(int parity, int mu, int h, double (&u)[18], R&) const {
-    load<false>(parity, mu, h, u);
+  __device__ __forceinline__ void load_scaled(int parity, int mu, int h, double (&u)[18], R& w) const {
+    load_scaled_slot<R8>(parity * 4 + mu, h, u, w);
   }
   template <bool R8>
   __device__ __forceinline__ void load(int parity, int mu, int h, double (&u)[18]) const {
+    load_slot(parity * 4 + mu, h, u);
+  }
+  // slot = parity * 4 + mu in a gauge field; a link face (one boundary
+  // slice of temporal links) has one slot per parity
+  template <bool R8, typename R>
+  __device__ __forceinline__ void load_scaled_slot(int slot, int h, double (&u)[18], R&) const {
+    load_slot(slot, h, u);
+  }
+  __device__ __forceinline__ void load_slot(int slot, int h, double (&u)[18]) const {
     const int nc = recon / 2;
-    const double2* b = p + (size_t)(parity * 4 + mu) * nc * stride + h;
+    const double2* b = p + (size_t)slot * nc * stride + h;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      double2 d = __ldcs(b + (size_t)c * stride);
+      double2 d = ld_link(b + (size_t)c * stride);
       u[2 * c] = d.x;
       u[2 * c + 1] = d.y;
     }
     if (recon == 18) {
 #pragma unroll
       for (int c = 6; c < 9; ++c) {
-        double2 d = __ldcs(b + (size_t)c * stride);
+        double2 d = ld_link(b + (size_t)c * stride);
         u[2 * c] = d.x;
         u[2 * c + 1] = d.y;
       }
@@ -537,21 +583,29 @@ struct GaugeF32 {
   // 12-real kernels carry none of the 8-number code)
   template <bool R8, typename R>
   __device__ __forceinline__ void load_scaled(int parity, int mu, int h, float (&u)[18], R&) const {
-    load<R8>(parity, mu, h, u);
+    load_slot<R8>(parity * 4 + mu, h, u);
   }
   template <bool R8>
   __device__ __forceinline__ void load(int parity, int mu, int h, float (&u)[18]) const {
+    load_slot<R8>(parity * 4 + mu, h, u);
+  }
+  template <bool R8, typename R>
+  __device__ __forceinline__ void load_scaled_slot(int slot, int h, float (&u)[18], R&) const {
+    load_slot<R8>(slot, h, u);
+  }
+  template <bool R8>
+  __device__ __forceinline__ void load_slot(int slot, int h, float (&u)[18]) const {
     if constexpr (R8) {
-      const float4* b = p + (size_t)(parity * 4 + mu) * 2 * stride + h;
-      const float4 d0 = __ldcs(b), d1 = __ldcs(b + stride);
+      const float4* b = p + (size_t)slot * 2 * stride + h;
+      const float4 d0 = ld_link(b), d1 = ld_link(b + stride);
       const float q[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
       su3_from8<false>(q, u);
       return;
     }
-    const float4* b = p + (size_t)(parity * 4 + mu) * 3 * stride + h;
+    const float4* b = p + (size_t)slot * 3 * stride + h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float4 d = __ldcs(b + (size_t)c * stride);
+      float4 d = ld_link(b + (size_t)c * stride);
       u[4 * c] = d.x;
       u[4 * c + 1] = d.y;
       u[4 * c + 2] = d.z;
@@ -577,7 +631,7 @@ struct Gauge16 {
   // point in every 16-bit format (code = rint(32767 angle / pi)); a2, a3, b1
   // use the format's own encoding.
   __device__ __forceinline__ void load8(int parity, int mu, int h, float (&u)[18]) const {
-    const uint4 a = __ldcs(p8 + (size_t)(parity * 4 + mu) * stride + h);
+    const uint4 a = ld_link(p8 + (size_t)(parity * 4 + mu) * stride + h);
     const uint32_t w[4] = {a.x, a.y, a.z, a.w};
     constexpr float kPiQ = 3.14159265358979f * kInv32767;
     float q[8];
@@ -603,15 +657,30 @@ struct Gauge16 {
     if constexpr (R8) {
       load8(parity, mu, h, u);
     } else {
-      load_raw(parity, mu, h, u);
+      load_raw_slot(parity * 4 + mu, h, u);
       if constexpr (F == Fmt16::Q16) w *= (R)kInv32767;
     }
   }
+  // a link face (12-real links only): slot = parity
+  template <bool R8, typename R>
+  __device__ __forceinline__ void load_scaled_slot(int slot, int h, float (&u)[18], R& w) const {
+    static_assert(!R8, "link faces hold 12-real links");
+    load_raw_slot(slot, h, u);
+    if constexpr (F == Fmt16::Q16) w *= (R)kInv32767;
+  }
   __device__ __forceinline__ void load_raw(int parity, int mu, int h, float (&u)[18]) const {
-    size_t o = (size_t)(parity * 4 + mu) * stride + h;
-    uint4 a = __ldcs(p8 + o);
-    uint2 b = __ldcs(p4 + o);
-    uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    load_raw_slot(parity * 4 + mu, h, u);
+  }
+  __device__ __forceinline__ void load_raw_slot(int slot, int h, float (&u)[18]) const {
+    size_t o = (size_t)slot * stride + h;
+    uint4 a = ld_link(p8 + o);
+    uint2 b = ld_link(p4 + o);
+    const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    from_words(w, u);
+  }
+  // the link from its 6 stored words (rows a, b): row c rebuilt, Q16 as raw
+  // codes (32767 U; the caller folds in 1/32767)
+  static __device__ __forceinline__ void from_words(const uint32_t (&w)[6], float (&u)[18]) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const float2 f = Spinor16<F>::pair(w[k]);

@@ -76,6 +76,15 @@ struct PrecOps {
   void (*batch_setup)(const Ctx&, const BatchLaunch&, BatchBufs&, cudaStream_t);
   void (*batch_iteration)(const Ctx&, const BatchLaunch&, BatchBufs&, cudaStream_t);
   void (*batch_update)(const Ctx&, const BatchLaunch&, BatchBufs&, cudaStream_t);
+  // T-slab decomposition (Sec. 6): projected boundary faces, the link face
+  // of the last slice, and the dslash of a slab region reading received halos
+  size_t (*slab_face_bytes)(const Ctx&);
+  size_t (*slab_link_face_bytes)(const Ctx&);
+  void (*slab_pack_faces)(const Ctx&, void* lo, void* hi, const void* in, int dagger, cudaStream_t);
+  void (*slab_pack_link_face)(const Ctx&, void* face, cudaStream_t);
+  void (*slab_dslash)(const Ctx&, void* out, const void* in, const void* halo_lo, const void* halo_hi,
+                      const void* link_halo, int flip_lo, int flip_hi, int parity, int dagger, int region,
+                      cudaStream_t);
 };
 
 const PrecOps* ops_f64();

@@ -12,6 +12,8 @@
 #pragma once
 
 #include "wd_internal.h"
+#include "wd_slab.cuh"
+#include "wd_async.cuh"
 
 namespace wd {
 
@@ -417,6 +419,34 @@ struct EpiResid {
   }
 };
 
+// x_o = b + c acc (stored) and, from the same acc, the odd rows of the true
+// residual of the stored x: r_o = b - (x_o - c acc), reduced as |r_o|^2 (the
+// expressions of EpiXpay and EpiResid, in FP64; Sec. 3: x_o is rebuilt from
+// x_e, and the residual of the returned x is computed from the same D_oe x_e)
+template <class Fin>
+struct EpiReconResid {
+  static constexpr int NRED = 1;
+  SpinorF64 out, b;
+  Coef c;
+  RedScratch rs;
+  Fin fin;
+  __device__ __forceinline__ void operator()(int h, double (&a)[24], double* red) const {
+    double bv[24];
+    b.load(h, bv);
+    const double cc = c.get(), ncc = -cc;
+    double n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+      const double y = bv[k] + cc * a[k];
+      const double r = bv[k] - (y + ncc * a[k]);
+      a[k] = y;
+      n += r * r;
+    }
+    out.store(h, a);
+    red[0] += n;
+  }
+};
+
 // BiCGstab reliable update: r = b_hat - (x + c acc) in FP64, r_hat = quantised
 // r; reduce |r|^2 (FP64), <r_tilde, r_hat>, |r_hat|^2
 template <class RH, class RT, class Fin>
@@ -490,6 +520,15 @@ struct DslashOccupancy {
                                                           : (NRED == 0 ? 5 : 4);
 };
 
+// 16-bit spinors with 12-real links take the cp.async pipeline of
+// wd_async.cuh (neighbour words staged through shared memory)
+constexpr bool kAsync16 = false;
+template <class In, bool R8>
+struct UseAsync {
+  static constexpr bool value = kAsync16 && In::kBytesPerSite == 52 && !R8;
+};
+static_assert(kDslashBlock == kAsyncBlock, "the async slots are sized for the dslash block");
+
 // TFIX: links in the temporal gauge; R8: FP32 / 16-bit links as the 8
 // numbers of App. A.2.  Both are compile-time variants selected at launch.
 template <bool DAGGER, bool TFIX, bool R8, typename R, class In, class G, class Epi>
@@ -502,7 +541,8 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
   for (int k = 0; k < NR; ++k) red[k] = 0.0;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
     R acc[24];
-    dslash_site<DAGGER, TFIX, R8, Epi::NRED == 0>(g, in, gauge, h, parity, acc);
+    if constexpr (UseAsync<In, R8>::value) dslash_site_async<DAGGER, TFIX>(g, in, gauge, h, parity, acc);
+    else dslash_site<DAGGER, TFIX, R8, Epi::NRED == 0>(g, in, gauge, h, parity, acc);
     epi(h, acc, red);
   }
   if constexpr (Epi::NRED > 0) grid_reduce<Epi::NRED>(red, epi.rs, epi.fin);
@@ -884,6 +924,21 @@ struct Tr<WD_F64> {
   static size_t bytes(int stride) { return align256(192 * (size_t)stride); }
   static S view(const void* p, const Geom& g, size_t rs = 0) { return S{(double2*)p, g.stride, rs}; }
   static G gauge(const Ctx& c) { return G{(const double2*)c.gauge[WD_F64], c.g.stride, c.recon}; }
+  // T-slab faces (wd_slab.cuh)
+  using Fc = FaceF64;
+  static size_t face_bytes(int fs) { return align256(96 * (size_t)fs); }
+  static Fc face(const void* p, int fs) { return Fc{(const double2*)p, fs}; }
+  static size_t link_face_bytes(const Ctx& c, int fs) { return align256((size_t)2 * (c.recon / 2) * 16 * fs); }
+  static LinkFace<G> link_face(const Ctx& c, const void* p, int fs) { return {G{(const double2*)p, fs, c.recon}}; }
+  static void pack_faces(const Ctx& c, void* lo, void* hi, const void* in, int fs, int dagger, int grid,
+                         cudaStream_t s) {
+    pack_faces_f64_kernel<<<grid, 256, 0, s>>>(c.g, (const double2*)in, c.g.stride, (double2*)lo, (double2*)hi, fs,
+                                               dagger);
+  }
+  static void pack_link_face(const Ctx& c, void* out, int fs, int grid, cudaStream_t s) {
+    pack_link_face_kernel<double2><<<grid, 256, 0, s>>>(c.g, (const double2*)c.gauge[WD_F64], c.recon / 2,
+                                                        c.g.stride, (double2*)out, fs);
+  }
 };
 template <>
 struct Tr<WD_F32> {
@@ -893,6 +948,20 @@ struct Tr<WD_F32> {
   static size_t bytes(int stride) { return align256(96 * (size_t)stride); }
   static S view(const void* p, const Geom& g, size_t rs = 0) { return S{(float4*)p, g.stride, rs}; }
   static G gauge(const Ctx& c) { return G{(const float4*)c.gauge[WD_F32], c.g.stride, c.low_recon}; }
+  using Fc = FaceF32;
+  static size_t face_bytes(int fs) { return align256(48 * (size_t)fs); }
+  static Fc face(const void* p, int fs) { return Fc{(const float4*)p, fs}; }
+  static size_t link_face_bytes(const Ctx&, int fs) { return align256((size_t)2 * 3 * 16 * fs); }
+  static LinkFace<G> link_face(const Ctx&, const void* p, int fs) { return {G{(const float4*)p, fs, 12}}; }
+  static void pack_faces(const Ctx& c, void* lo, void* hi, const void* in, int fs, int dagger, int grid,
+                         cudaStream_t s) {
+    pack_faces_f32_kernel<<<grid, 256, 0, s>>>(c.g, (const float4*)in, c.g.stride, (float4*)lo, (float4*)hi, fs,
+                                               dagger);
+  }
+  static void pack_link_face(const Ctx& c, void* out, int fs, int grid, cudaStream_t s) {
+    pack_link_face_kernel<float4><<<grid, 256, 0, s>>>(c.g, (const float4*)c.gauge[WD_F32], 3, c.g.stride,
+                                                       (float4*)out, fs);
+  }
 };
 template <Fmt16 F, int P>
 struct Tr16 {
@@ -905,6 +974,36 @@ struct Tr16 {
   }
   static G gauge(const Ctx& c) {
     return G{(const uint4*)c.gauge[P], (const uint2*)c.gauge4[P], c.g.stride, c.low_recon};
+  }
+  using Fc = Face16<F>;
+  static size_t face_bytes(int fs) {
+    return align256(16 * (size_t)fs) + align256(8 * (size_t)fs) + align256(4 * (size_t)fs);
+  }
+  static Fc face(const void* p, int fs) {
+    const char* b = (const char*)p;
+    return Fc{(const uint4*)b, (const uint2*)(b + align256(16 * (size_t)fs)),
+              (const float*)(b + align256(16 * (size_t)fs) + align256(8 * (size_t)fs)), fs};
+  }
+  static size_t link_face_bytes(const Ctx&, int fs) { return align256(32 * (size_t)fs) + align256(16 * (size_t)fs); }
+  static LinkFace<G> link_face(const Ctx&, const void* p, int fs) {
+    const char* b = (const char*)p;
+    return {G{(const uint4*)b, (const uint2*)(b + align256(32 * (size_t)fs)), fs, 12}};
+  }
+  static void pack_faces(const Ctx& c, void* lo, void* hi, const void* in, int fs, int dagger, int grid,
+                         cudaStream_t s) {
+    const size_t ob = align256(16 * (size_t)fs), on = ob + align256(8 * (size_t)fs);
+    char* l = (char*)lo;
+    char* h = (char*)hi;
+    pack_faces_16_kernel<<<grid, 256, 0, s>>>(c.g, (const uint4*)in,
+                                              (const float*)((const char*)in + align256(48 * (size_t)c.g.stride)),
+                                              c.g.stride, (uint4*)l, (uint2*)(l + ob), (float*)(l + on), (uint4*)h,
+                                              (uint2*)(h + ob), (float*)(h + on), fs, dagger);
+  }
+  static void pack_link_face(const Ctx& c, void* out, int fs, int grid, cudaStream_t s) {
+    char* o = (char*)out;
+    pack_link_face_kernel<uint4><<<grid, 256, 0, s>>>(c.g, (const uint4*)c.gauge[P], 1, c.g.stride, (uint4*)o, fs);
+    pack_link_face_kernel<uint2><<<grid, 256, 0, s>>>(c.g, (const uint2*)c.gauge4[P], 1, c.g.stride,
+                                                      (uint2*)(o + align256(32 * (size_t)fs)), fs);
   }
 };
 template <>
@@ -1155,6 +1254,39 @@ struct Impl {
     launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 1, e2, s);
   }
 
+  // ---- T-slab decomposition (Sec. 6): faces and the split dslash
+  static size_t slab_face_bytes(const Ctx& c) { return T::face_bytes(face_stride(c.g)); }
+  static size_t slab_link_face_bytes(const Ctx& c) { return T::link_face_bytes(c, face_stride(c.g)); }
+  static void slab_pack_faces(const Ctx& c, void* lo, void* hi, const void* in, int dagger, cudaStream_t s) {
+    const int grid = wave_grid(2 * c.g.XhYZ, 256, c.num_sms, 8);
+    T::pack_faces(c, lo, hi, in, face_stride(c.g), dagger, grid, s);
+  }
+  static void slab_pack_link_face(const Ctx& c, void* face, cudaStream_t s) {
+    const int grid = wave_grid(2 * c.g.XhYZ * 9, 256, c.num_sms, 8);
+    T::pack_link_face(c, face, face_stride(c.g), grid, s);
+  }
+  static void slab_dslash(const Ctx& c, void* out, const void* in, const void* halo_lo, const void* halo_hi,
+                          const void* link_halo, int flip_lo, int flip_hi, int parity, int dagger, int region,
+                          cudaStream_t s) {
+    const int fs = face_stride(c.g);
+    const SlabRegion reg{region, c.g.XhYZ, c.g.T, c.g.Vh};
+    const int n = reg.count();
+    if (n <= 0) return;
+    EpiStore<S> e{T::view(out, c.g)};
+    const auto lf = T::link_face(c, link_halo, fs);
+    const auto flo = T::face(halo_lo, fs), fhi = T::face(halo_hi, fs);
+    auto go = [&](auto dag) {
+      auto* k = dslash_slab_kernel<decltype(dag)::value, R, S, typename T::G, typename T::Fc, decltype(lf),
+                                   EpiStore<S>>;
+      static const int per_sm = resident_blocks(k, kDslashBlock);
+      const int grid = wave_grid(n, kDslashBlock, c.num_sms, per_sm);
+      k<<<grid, kDslashBlock, 0, s>>>(c.g, T::view(in, c.g), T::gauge(c), flo, fhi, lf, flip_lo, flip_hi, parity, reg,
+                                      e);
+    };
+    if (dagger) go(std::true_type{});
+    else go(std::false_type{});
+  }
+
   static PrecOps make() {
     PrecOps o{};
     o.prec = (wd_prec)P;
@@ -1173,6 +1305,11 @@ struct Impl {
     o.cg_iteration = &cg_iteration;
     o.cg_update = &cg_update;
     o.cg_setup = &cg_setup;
+    o.slab_face_bytes = &slab_face_bytes;
+    o.slab_link_face_bytes = &slab_link_face_bytes;
+    o.slab_pack_faces = &slab_pack_faces;
+    o.slab_pack_link_face = &slab_pack_link_face;
+    o.slab_dslash = &slab_dslash;
     return o;
   }
 };

@@ -22,8 +22,14 @@ t = T - 1 <-> 0 an antiperiodic time direction multiplies the halo by -1.
 
 The exchange uses torch.distributed point-to-point messages (gloo on CPU,
 NCCL on GPUs); with one rank the halos are the rank's own opposite slices.
-This module holds no compute of the stencil itself: the caller applies its
-own dslash to the extended slab.
+
+On the GPU (``SlabDslash``) the library packs the projected faces and runs the
+stencil: faces are packed by a kernel (``wd_slab_pack_faces``), travel on a
+communication stream into buffers in the receiving GPU's own memory, and the
+interior slices are computed while they travel (``wd_dslash_slab`` region 0);
+the two boundary slices follow once the halos have arrived (region 1).  The
+numpy functions below are the host-side form of the same exchange, used with
+the CPU oracle.
 """
 from __future__ import annotations
 
@@ -58,23 +64,53 @@ def halo_signs(rank: int, world: int, antiperiodic: bool) -> tuple[float, float]
     return lo, hi
 
 
-def _exchange(lo_send: np.ndarray, hi_send: np.ndarray, rank: int, world: int):
-    """Send lo_send to the lower neighbour and hi_send to the upper one;
-    return (from the lower neighbour, from the upper neighbour)."""
+def exchange_faces(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, group=None) -> None:
+    """Move torch tensors between time neighbours: send_lo (my first slice's
+    face) to the lower neighbour, where it arrives as its recv_hi; send_hi (my
+    last slice's face) to the upper neighbour, where it arrives as its
+    recv_lo.  One rank: the halos are my own opposite faces (a copy).
+
+    The messages are posted in one fixed order on every rank -- upward (hi to
+    the upper neighbour, lo halo from the lower one), then downward -- with
+    tag 0 for the upward and 1 for the downward direction.  Backends that
+    match point-to-point messages between a pair of ranks in posting order
+    (NCCL) then pair them correctly even with two ranks, where the lower and
+    upper neighbour are the same rank; gloo matches on the tags.  Returns once
+    the transfers are complete (CPU tensors) or, for CUDA tensors, once the
+    current stream is ordered after them."""
     if world == 1:
-        return hi_send.copy(), lo_send.copy()
-    import torch
+        recv_lo.copy_(send_hi)
+        recv_hi.copy_(send_lo)
+        return
     import torch.distributed as dist
     down, up = (rank - 1) % world, (rank + 1) % world
+    ops = [dist.P2POp(dist.isend, send_hi, up, group, tag=0), dist.P2POp(dist.irecv, recv_lo, down, group, tag=0),
+           dist.P2POp(dist.isend, send_lo, down, group, tag=1), dist.P2POp(dist.irecv, recv_hi, up, group, tag=1)]
+    for q in dist.batch_isend_irecv(ops):
+        q.wait()
+
+
+def send_up(send, recv, rank: int, world: int, group=None) -> None:
+    """send (my last slice's link face) to the upper neighbour; recv <- the
+    lower neighbour's.  One rank: a copy."""
+    if world == 1:
+        recv.copy_(send)
+        return
+    import torch.distributed as dist
+    down, up = (rank - 1) % world, (rank + 1) % world
+    ops = [dist.P2POp(dist.isend, send, up, group, tag=2), dist.P2POp(dist.irecv, recv, down, group, tag=2)]
+    for q in dist.batch_isend_irecv(ops):
+        q.wait()
+
+
+def _exchange(lo_send: np.ndarray, hi_send: np.ndarray, rank: int, world: int):
+    """numpy form of exchange_faces: returns (from the lower neighbour, from
+    the upper neighbour)."""
+    import torch
     t_lo = torch.from_numpy(np.ascontiguousarray(lo_send).view(np.float64).copy())
     t_hi = torch.from_numpy(np.ascontiguousarray(hi_send).view(np.float64).copy())
     r_lo, r_hi = torch.empty_like(t_hi), torch.empty_like(t_lo)
-    # tag 0: a lower halo travelling up; tag 1: an upper halo travelling down
-    # (with two ranks the lower and upper neighbour are the same rank)
-    reqs = [dist.isend(t_lo, down, tag=1), dist.isend(t_hi, up, tag=0),
-            dist.irecv(r_lo, down, tag=0), dist.irecv(r_hi, up, tag=1)]
-    for q in reqs:
-        q.wait()
+    exchange_faces(t_lo, t_hi, r_lo, r_hi, rank, world)
     shape = lo_send.shape
     return r_lo.numpy().view(np.complex128).reshape(shape), r_hi.numpy().view(np.complex128).reshape(shape)
 
@@ -105,3 +141,71 @@ def extended_parity(global_parity: int, t0: int) -> int:
     """Parity, in the extended slab (one halo slice below), of a site of the
     given global parity: the local time index is t - t0 + 1."""
     return global_parity ^ ((1 - t0) & 1)
+
+
+class SlabDslash:
+    """The dslash of one rank's T-slab on its GPU, with the face exchange.
+
+    ``wd`` is the rank's ``WilsonDirac`` context, created with the slab's dims
+    ``(X, Y, Z, nt)`` and loaded with the slab's links; ``rank`` / ``world``
+    place the slab at t0 = rank * nt of a lattice of T = world * nt slices.
+    With ``world`` > 1 the faces travel by torch.distributed (the process
+    group must be initialised: NCCL for CUDA tensors).  One apply():
+
+    1. pack both projected faces of the input (library stream);
+    2. on the communication stream, after the pack: exchange the faces into
+       this GPU's halo buffers;
+    3. meanwhile, on the library stream: the interior slices (region 0);
+    4. the library stream waits for the exchange, then the two boundary
+       slices (region 1).
+    """
+
+    def __init__(self, wd, rank: int, world: int, t_antiperiodic: bool = False, group=None, overlap: bool = True):
+        import torch
+        self.wd, self.rank, self.world, self.group = wd, rank, world, group
+        self.torch = torch
+        lo_sign, hi_sign = halo_signs(rank, world, t_antiperiodic)
+        self.flip_lo, self.flip_hi = lo_sign < 0, hi_sign < 0
+        self.overlap = overlap
+        self.comm = torch.cuda.Stream() if overlap else wd.stream
+        self._faces = {}
+        self._links = {}
+
+    def _buf(self, n):
+        return self.torch.empty(n, dtype=self.torch.uint8, device="cuda")
+
+    def faces(self, prec: int):
+        """(send_lo, send_hi, halo_lo, halo_hi) device buffers of one precision."""
+        if prec not in self._faces:
+            n = self.wd.slab_face_bytes(prec)
+            self._faces[prec] = tuple(self._buf(n) for _ in range(4))
+        return self._faces[prec]
+
+    def link_halo(self, prec: int):
+        """The lower neighbour's link face (exchanged once per precision)."""
+        if prec not in self._links:
+            n = self.wd.slab_link_face_bytes(prec)
+            send, recv = self._buf(n), self._buf(n)
+            self.wd.slab_pack_link_face(send, prec)
+            s = self.wd.stream
+            with self.torch.cuda.stream(s):
+                send_up(send, recv, self.rank, self.world, self.group)
+            self._links[prec] = (send, recv)
+        return self._links[prec][1]
+
+    def apply(self, out, inp, out_parity: int, dagger: bool, prec: int):
+        torch = self.torch
+        wd, s = self.wd, self.wd.stream
+        link = self.link_halo(prec)
+        send_lo, send_hi, halo_lo, halo_hi = self.faces(prec)
+        wd.slab_pack_faces(send_lo, send_hi, inp, dagger, prec)
+        packed = torch.cuda.Event()
+        packed.record(s)
+        with torch.cuda.stream(self.comm):
+            self.comm.wait_event(packed)
+            exchange_faces(send_lo, send_hi, halo_lo, halo_hi, self.rank, self.world, self.group)
+            arrived = torch.cuda.Event()
+            arrived.record(self.comm)
+        wd.dslash_slab(out, inp, None, None, None, False, False, out_parity, dagger, prec, 0)
+        s.wait_event(arrived)
+        wd.dslash_slab(out, inp, halo_lo, halo_hi, link, self.flip_lo, self.flip_hi, out_parity, dagger, prec, 1)

@@ -47,7 +47,14 @@ def test_reference_arm_json_contract(monkeypatch, capsys):
         assert key in line, key
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "solves/s"
     assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
-    assert line["value"] > 0 and line["ms_per_step"] == pytest.approx(1000.0 / line["value"])
+    # a step is the sampled part of a solve, timed as it ran; value extrapolates
+    # it to whole solves by the stated factor
+    cb0 = line["cpu_baseline"]
+    assert line["ms_per_step"] == pytest.approx(1000.0 * cb0["sample_seconds"], rel=1e-3)
+    assert line["value"] == pytest.approx(cb0["sample_iterations"] / (cb0["sample_seconds"] * cb0["full_solve_iterations"]),
+                                          rel=1e-2)
+    assert cb0["extrapolated"] and cb0["scale"] == pytest.approx(cb0["full_solve_iterations"] / cb0["sample_iterations"],
+                                                                 rel=1e-3)
     assert line["config"]["workload"] == bench.WORKLOAD["workload"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]

@@ -96,3 +96,48 @@ def test_slab_ranges():
     assert [tslab.slab_range(12, 3, r) for r in range(3)] == [(0, 4), (4, 4), (8, 4)]
     with pytest.raises(ValueError):
         tslab.slab_range(12, 4, 0)  # slabs of 3 slices: odd
+
+
+def _exchange_rank(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_0911_3191_gb300 import tslab
+    # distinct contents per rank and per face
+    send_lo = torch.full((5,), 100.0 * rank + 1.0, dtype=torch.float64)
+    send_hi = torch.full((5,), 100.0 * rank + 2.0, dtype=torch.float64)
+    recv_lo, recv_hi = torch.zeros(5, dtype=torch.float64), torch.zeros(5, dtype=torch.float64)
+    tslab.exchange_faces(send_lo, send_hi, recv_lo, recv_hi, rank, world)
+    link_send = torch.full((3,), 100.0 * rank + 7.0, dtype=torch.float64)
+    link_recv = torch.zeros(3, dtype=torch.float64)
+    tslab.send_up(link_send, link_recv, rank, world)
+    out[rank] = (recv_lo[0].item(), recv_hi[0].item(), link_recv[0].item())
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4])
+def test_face_exchange_reaches_the_right_neighbours(world):
+    """The exchange the GPU slab path uses (exchange_faces, send_up), on gloo
+    ranks: each rank's lower halo is its lower neighbour's last-slice face,
+    its upper halo the upper neighbour's first-slice face, its link halo the
+    lower neighbour's link face (periodic in the rank index; with two ranks
+    both neighbours are the same rank)."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    if world == 1:
+        _exchange_rank(0, 1, port, out)
+    else:
+        procs = [ctx.Process(target=_exchange_rank, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+    for r in range(world):
+        below, above = (r - 1) % world, (r + 1) % world
+        assert out[r] == (100.0 * below + 2.0, 100.0 * above + 1.0, 100.0 * below + 7.0), (world, r, out[r])
