@@ -70,12 +70,34 @@ FLOPS_PER_SITE = 1320  # the paper's effective count (Sec. 4.3)
 # the unit count agrees: 2 FP64 FMA lanes per SM per clock x 2 flops x 152 SMs
 # x 2.07 GHz = 1.259 TFLOP/s
 FP64_PEAK_TFLOPS = 1.252
-# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu capture of the current kernel (ncu --set full of the dslash-only
-# command of this file); an entry is removed when its kernel changes.
-# key: (precision, link reals, lattice, temporal gauge)
-NCU_TRAFFIC_BYTES = {("f64", 18, "24x24x24x64", True): 526.07e6,
-                     ("q16", 12, "24x24x24x64", True): 90.98e6}
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from an ncu capture of the dslash-only command of this file, keyed by
+# (precision, link reals, lattice, temporal gauge).  KERNEL_SOURCES_SHA is the
+# hash of the kernel sources the counters were taken on (kernel_sources_sha());
+# when the sources differ, the bench reports traffic as null.
+KERNEL_SOURCES_SHA = ""
+NCU_TRAFFIC_BYTES = {}
+
+
+def kernel_sources_sha() -> str:
+    """sha256 (16 hex digits) of the CUDA sources that define the dslash kernels."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_0911_3191_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "wd_prec_*.cu"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """The recorded DRAM traffic of a kernel, or None when the kernel sources
+    changed since it was captured."""
+    if not KERNEL_SOURCES_SHA or kernel_sources_sha() != KERNEL_SOURCES_SHA:
+        return None
+    return NCU_TRAFFIC_BYTES.get(key)
 PREC_NAME = {0: "f64", 1: "f32", 2: "q16", 3: "h16n", 4: "b16n"}
 ORACLE_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_fp64_iterations.json")
 
@@ -378,10 +400,11 @@ def run_ours(args):
     t64 = time_dslash(wd, torch, wdp.F64, 20, flush=flush, psi=b)
     tf = args.temporal_gauge
     f64_tflops = flops_per_site(tf) * vh / t64 / 1e12
-    traffic = NCU_TRAFFIC_BYTES.get(("f64", args.recon, "x".join(map(str, dims)), tf))
+    traffic = ncu_traffic(("f64", args.recon, "x".join(map(str, dims)), tf))
     roofline = {"bound": "alu", "achieved": round(f64_tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(f64_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "algorithmic_bytes": bytes_per_site(0, args.recon, tf) * vh, "peak_source": "measured FP64 FMA",
+                "kernel_sources_sha": kernel_sources_sha(),
                 "kernel": f"dslash f64 {args.recon}-real (reliable update){' temporal gauge' if tf else ''}, "
                           f"{dims[0]}^3x{dims[3]}, {vh} sites/launch, {flops_per_site(tf)} flops/site",
                 "us_per_launch": round(t64 * 1e6, 2)}
@@ -390,7 +413,7 @@ def run_ours(args):
     achieved = bytes_per_site(inner, 12, tf, args.recon8) * vh / t_ds / 1e9
     dslash_roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                        "frac": round(achieved / hbm, 4),
-                       "traffic": NCU_TRAFFIC_BYTES.get((args.inner, 8 if args.recon8 else 12, "x".join(map(str, dims)), tf)),
+                       "traffic": ncu_traffic((args.inner, 8 if args.recon8 else 12, "x".join(map(str, dims)), tf)),
                        "peak_source": src,
                        "kernel": f"dslash {args.inner} {'8-number' if args.recon8 else '12-real'} (inner iteration), "
                                  f"{dims[0]}^3x{dims[3]}, {vh} "
@@ -811,6 +834,9 @@ def run_batch(args):
             r += 1
     fx = wd.new_field(wdp.F64, 2 * n)
     s = wd.stream
+    # the autotuner writes its choice (RHS tile, grid, packed layout) to this cache
+    tune_file = tempfile.NamedTemporaryFile(prefix="wd_tune_", suffix=".txt", delete=False).name
+    os.environ["WD_TUNE_CACHE"] = tune_file
     t0 = time.perf_counter()
     infos = wd.solve_batch_device(fx, fb, ks, tol=1e-12, inner_precision=inner)  # includes the autotuning
     first_s = time.perf_counter() - t0
@@ -891,8 +917,14 @@ def run_batch(args):
     mrhs["f64_batched16_us"] = round(1e6 * statistics.mean(d64["batched"]), 1)
     mrhs["f64_single_x16_us"] = round(1e6 * statistics.mean(d64["single"]), 1)
     del f64in, f64out
+    try:
+        shape = open(tune_file).read().strip().split("|")[-1].split()
+        tuned = {"rhs_tile": int(shape[0]), "grid": int(shape[1]), "packed_pairs": bool(int(shape[2]))}
+    except Exception:
+        tuned = None
+    os.unlink(tune_file)
     print(json.dumps({"batch": "32x32x32x64, 12 point sources x 4 kappa", "n_systems": n, "inner": args.inner,
-                      "temporal_gauge": args.temporal_gauge,
+                      "temporal_gauge": args.temporal_gauge, "tuned_shape": tuned,
                       "mrhs_dslash": mrhs,
                       "fp64_link_reals": args.recon, "s_per_batched_solve": round(t_batch, 4),
                       "systems_per_s": round(n / t_batch, 3), "s_first_call_incl_tuning": round(first_s, 3),

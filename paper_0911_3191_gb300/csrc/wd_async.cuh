@@ -10,7 +10,9 @@
 // holding any register; the arithmetic is that of hop() and hop_t() (the
 // same decoders, projections, SU(3) products and reconstructions, in the
 // same order).  Copies are ordered per thread: no thread reads another's
-// slots, so no barrier is needed.
+// slots, so no barrier is needed.  16-byte spinor words bypass L1 (.cg: the
+// slots take most of the SM's shared memory and L1 is small); link words go
+// with an L2 evict-first policy.
 #pragma once
 
 #include "wd_device.cuh"
@@ -18,11 +20,25 @@
 namespace wd {
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp16_ca(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp16_cg(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// link words are read once per dslash: copies with an L2 evict-first policy,
+// so that they do not displace the neighbour spinors that other sites reuse
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp16_cg_ef(void* dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp8_ca_ef(void* dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ void cp8_ca(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -63,15 +79,15 @@ __device__ __forceinline__ void async_issue(AsyncSlots& sm, const In& in, const 
   const size_t st = (size_t)in.stride;
   if constexpr (H::MU < 3) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) cp16_ca(&sm.sp[H::ST][c][tid], in.p + c * st + n);
+    for (int c = 0; c < 3; ++c) cp16_cg(&sm.sp[H::ST][c][tid], in.p + c * st + n);
   } else {
     constexpr int S = (H::FWD != DAGGER) ? -1 : +1;
     if constexpr (S == +1) {  // spins 0, 1: chunk 0 and the first half of chunk 1
-      cp16_ca(&sm.sp[H::ST][0][tid], in.p + n);
+      cp16_cg(&sm.sp[H::ST][0][tid], in.p + n);
       cp8_ca(&sm.sp[H::ST][1][tid], reinterpret_cast<const uint2*>(in.p + st + n));
     } else {  // spins 2, 3: the second half of chunk 1 and chunk 2
       cp8_ca(&sm.sp[H::ST][0][tid], reinterpret_cast<const uint2*>(in.p + st + n) + 1);
-      cp16_ca(&sm.sp[H::ST][1][tid], in.p + 2 * st + n);
+      cp16_cg(&sm.sp[H::ST][1][tid], in.p + 2 * st + n);
     }
   }
   cp4_ca(&sm.sn[H::ST][tid], in.norm + n);
@@ -80,8 +96,9 @@ __device__ __forceinline__ void async_issue(AsyncSlots& sm, const In& in, const 
   if (!unit) {
     const int slot = (H::FWD ? parity : 1 - parity) * 4 + H::MU;
     const size_t o = (size_t)slot * gauge.stride + (H::FWD ? h : n);
-    cp16_cg(&sm.l4[H::ST][tid], gauge.p8 + o);
-    cp8_ca(&sm.l2[H::ST][tid], gauge.p4 + o);
+    const uint64_t pol = l2_evict_first();
+    cp16_cg_ef(&sm.l4[H::ST][tid], gauge.p8 + o, pol);
+    cp8_ca_ef(&sm.l2[H::ST][tid], gauge.p4 + o, pol);
   }
 }
 

@@ -139,6 +139,160 @@ constexpr size_t tile_link_bytes() {
   return (size_t)8 * 18 * 32 * sizeof(R);
 }
 
+// ---- two right-hand sides per thread in FP32x2 registers.  The systems of a
+// pair share every link, so the SU(3) products, the reconstructions and the
+// accumulators run as packed (sm_100 family) FMA2 operations on (system a,
+// system b); the tile holds each link value as a broadcast pair (u, u), read
+// with one 64-bit shared load.  Decoding and projection stay per system.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fms2(float2 a, float2 b, float2 c) {  // c - a b
+  return __ffma2_rn(make_float2(-a.x, -a.y), b, c);
+}
+
+// g = U h (DAG false) or U^dag h, both spin rows; u: the link's 18 values as
+// pairs at u[k * 32]
+template <bool DAG>
+__device__ __forceinline__ void su3_mul2(const float2* u, const float2 (&h)[12], float2 (&g)[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) g[k] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int e = DAG ? (j * 3 + i) : (i * 3 + j);
+      const float2 ur = u[(2 * e) * 32], ui = u[(2 * e + 1) * 32];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const float2 hr = h[(s * 3 + j) * 2], hi = h[(s * 3 + j) * 2 + 1];
+        float2& re = g[(s * 3 + i) * 2];
+        float2& im = g[(s * 3 + i) * 2 + 1];
+        if constexpr (DAG) {  // conj(U_ji) h_j
+          re = fma2(ur, hr, re);
+          re = fma2(ui, hi, re);
+          im = fma2(ur, hi, im);
+          im = fms2(ui, hr, im);
+        } else {  // U_ij h_j
+          re = fma2(ur, hr, re);
+          re = fms2(ui, hi, re);
+          im = fma2(ur, hi, im);
+          im = fma2(ui, hr, im);
+        }
+      }
+    }
+  }
+}
+
+// reconstruct_scaled() on pairs: a += w P g for both systems
+template <int MU, int S_>
+__device__ __forceinline__ void reconstruct_scaled2(const float2 (&g)[12], float2 (&a)[24], float2 w) {
+  constexpr int S = (MU == 1) ? -S_ : S_;
+  const float2 ws = (S > 0) ? w : make_float2(-w.x, -w.y);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 g0r = g[c * 2], g0i = g[c * 2 + 1];
+    const float2 g1r = g[(3 + c) * 2], g1i = g[(3 + c) * 2 + 1];
+    a[(0 + c) * 2] = fma2(w, g0r, a[(0 + c) * 2]);
+    a[(0 + c) * 2 + 1] = fma2(w, g0i, a[(0 + c) * 2 + 1]);
+    a[(3 + c) * 2] = fma2(w, g1r, a[(3 + c) * 2]);
+    a[(3 + c) * 2 + 1] = fma2(w, g1i, a[(3 + c) * 2 + 1]);
+    if constexpr (MU == 0) {
+      a[(6 + c) * 2] = fma2(ws, g1i, a[(6 + c) * 2]);
+      a[(6 + c) * 2 + 1] = fms2(ws, g1r, a[(6 + c) * 2 + 1]);
+      a[(9 + c) * 2] = fma2(ws, g0i, a[(9 + c) * 2]);
+      a[(9 + c) * 2 + 1] = fms2(ws, g0r, a[(9 + c) * 2 + 1]);
+    } else if constexpr (MU == 1) {
+      a[(6 + c) * 2] = fma2(ws, g1r, a[(6 + c) * 2]);
+      a[(6 + c) * 2 + 1] = fma2(ws, g1i, a[(6 + c) * 2 + 1]);
+      a[(9 + c) * 2] = fms2(ws, g0r, a[(9 + c) * 2]);
+      a[(9 + c) * 2 + 1] = fms2(ws, g0i, a[(9 + c) * 2 + 1]);
+    } else {
+      a[(6 + c) * 2] = fma2(ws, g0i, a[(6 + c) * 2]);
+      a[(6 + c) * 2 + 1] = fms2(ws, g0r, a[(6 + c) * 2 + 1]);
+      a[(9 + c) * 2] = fms2(ws, g1i, a[(9 + c) * 2]);
+      a[(9 + c) * 2 + 1] = fma2(ws, g1r, a[(9 + c) * 2 + 1]);
+    }
+  }
+}
+
+// decode + project one system's neighbour (as hop_tile does), w its scale
+template <int MU, int S, class In>
+__device__ __forceinline__ float project_one(const In& in, int h_nbr, float (&hs)[12]) {
+  float psi[24];
+  float w = 1.f;
+  if constexpr (In::kScaled) w = in.load_raw(h_nbr, psi);
+  else in.load(h_nbr, psi);
+  project<MU, S>(psi, hs);
+  return w;
+}
+
+template <int MU, bool FWD, bool DAGGER, class In>
+__device__ __forceinline__ void hop_tile2(const In& ina, const In& inb, const float2* lk2, int sx, int h_nbr,
+                                          float2 (&acc)[24]) {
+  constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  constexpr int which = 2 * MU + (FWD ? 0 : 1);
+  float2 h2[12];
+  float2 w;
+  {
+    float ha[12], hb[12];
+    w.x = project_one<MU, S>(ina, h_nbr, ha);
+    w.y = project_one<MU, S>(inb, h_nbr, hb);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) h2[k] = make_float2(ha[k], hb[k]);
+  }
+  float2 g2[12];
+  su3_mul2<!FWD>(lk2 + which * 18 * 32 + sx, h2, g2);
+  reconstruct_scaled2<MU, S>(g2, acc, w);
+}
+
+template <bool FWD, bool DAGGER, class In>
+__device__ __forceinline__ void hop_tile2_t(const In& ina, const In& inb, const float2* lk2, int sx, int h_nbr,
+                                            bool flip, bool unit, float2 (&acc)[24]) {
+  constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  constexpr bool upper = (S == +1);
+  constexpr int which = 6 + (FWD ? 0 : 1);
+  constexpr int o = upper ? 0 : 12;
+  float2 h2[12];
+  float2 w = make_float2(1.f, 1.f);
+  {
+    float ha[12], hb[12];
+    if constexpr (In::kScaled) {
+      w.x = ina.load_raw_half(h_nbr, upper, ha);
+      w.y = inb.load_raw_half(h_nbr, upper, hb);
+    } else {
+      ina.load_half(h_nbr, upper, ha);
+      inb.load_half(h_nbr, upper, hb);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) h2[k] = make_float2(ha[k], hb[k]);
+  }
+  const float2 w2 = flip ? make_float2(-2.f * w.x, -2.f * w.y) : make_float2(2.f * w.x, 2.f * w.y);
+  if (unit) {  // temporal gauge: the link is 1
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[o + k] = fma2(w2, h2[k], acc[o + k]);
+    return;
+  }
+  float2 g2[12];
+  su3_mul2<!FWD>(lk2 + which * 18 * 32 + sx, h2, g2);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[o + k] = fma2(w2, g2[k], acc[o + k]);
+}
+
+template <bool DAGGER, class In>
+__device__ __forceinline__ void dslash_site_tile2(const In& ina, const In& inb, const float2* lk2, int sx,
+                                                  const int (&nb)[8], bool top, bool bot, bool unit_fwd,
+                                                  bool unit_bwd, float2 (&acc)[24]) {
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] = make_float2(0.f, 0.f);
+  hop_tile2<0, true, DAGGER>(ina, inb, lk2, sx, nb[0], acc);
+  hop_tile2<0, false, DAGGER>(ina, inb, lk2, sx, nb[1], acc);
+  hop_tile2<1, true, DAGGER>(ina, inb, lk2, sx, nb[2], acc);
+  hop_tile2<1, false, DAGGER>(ina, inb, lk2, sx, nb[3], acc);
+  hop_tile2<2, true, DAGGER>(ina, inb, lk2, sx, nb[4], acc);
+  hop_tile2<2, false, DAGGER>(ina, inb, lk2, sx, nb[5], acc);
+  hop_tile2_t<true, DAGGER>(ina, inb, lk2, sx, nb[6], top, unit_fwd, acc);
+  hop_tile2_t<false, DAGGER>(ina, inb, lk2, sx, nb[7], bot, unit_bwd, acc);
+}
+
 // Multi-RHS dslash: block (32 sites) x (TR right-hand sides), grid-stride over
 // 32-site tiles; dynamic shared memory = links + nrhs * NRED doubles.
 template <bool DAGGER, typename R, class In, class G, class Epi, int TR>
@@ -216,6 +370,113 @@ __global__ void __launch_bounds__(32 * TR) dslash_mrhs_kernel(Geom g, In in, G g
   }
 }
 
+// Multi-RHS dslash with two systems per thread (FP32 and 16-bit storage):
+// block (32 sites) x (TP pairs of right-hand sides), grid-stride over 32-site
+// tiles; dynamic shared memory = links as broadcast pairs + nrhs * NRED
+// doubles.  An unpaired or inactive system of a pair rides along on its
+// partner's data and writes nothing.
+template <typename R>
+constexpr size_t tile_link_bytes2() {
+  return (size_t)8 * 18 * 32 * sizeof(float2);
+}
+
+template <bool DAGGER, class In, class G, class Epi, int TP>
+__global__ void __launch_bounds__(32 * TP) dslash_mrhs2_kernel(Geom g, In in, G gauge, int parity, Epi epi,
+                                                               BatchArgs ba) {
+  pdl_wait();
+  constexpr int NR = Epi::NRED > 0 ? Epi::NRED : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* lk2 = reinterpret_cast<float2*>(smem_raw);
+  double* sred = reinterpret_cast<double*>(smem_raw + tile_link_bytes2<float>());
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if constexpr (Epi::NRED > 0)
+    for (int i = tid; i < ba.nrhs * NR; i += 32 * TP) sred[i] = 0.0;
+  const int ntiles = (g.Vh + 31) / 32;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();  // the previous tile's links are no longer read
+    for (int id = tid; id < 256; id += 32 * TP) {
+      const int which = id >> 5, sx = id & 31, hs = tile * 32 + sx;
+      if (hs < g.Vh) {
+        int x, y, z, t;
+        site_coords(g, hs, parity, x, y, z, t);
+        int nb[8];
+        neighbours(g, hs, x, y, z, t, nb);
+        const int mu = which >> 1;
+        const bool fwd = (which & 1) == 0;
+        if (g.tfix && mu == 3 && (fwd ? t != g.T - 1 : t != 0)) continue;
+        float u[18];
+        if (gauge.recon == 8) gauge.template load<true>(fwd ? parity : 1 - parity, mu, fwd ? hs : nb[which], u);
+        else gauge.template load<false>(fwd ? parity : 1 - parity, mu, fwd ? hs : nb[which], u);
+#pragma unroll
+        for (int k = 0; k < 18; ++k) lk2[(which * 18 + k) * 32 + sx] = make_float2(u[k], u[k]);
+      }
+    }
+    __syncthreads();
+    const int h = tile * 32 + threadIdx.x;
+    const bool site_ok = h < g.Vh;
+    int nb[8];
+    bool top = false, bot = false, unit_fwd = false, unit_bwd = false;
+    if (site_ok) {
+      int x, y, z, t;
+      site_coords(g, h, parity, x, y, z, t);
+      neighbours(g, h, x, y, z, t, nb);
+      top = g.tbc_anti && (t == g.T - 1);
+      bot = g.tbc_anti && (t == 0);
+      unit_fwd = g.tfix && (t != g.T - 1);
+      unit_bwd = g.tfix && (t != 0);
+    }
+    const bool listed = ba.mode == 1 && ba.bc;
+    const int nwork = listed ? *(const volatile int*)&ba.bc->nupd : ba.nrhs;
+    for (int r0 = 0; r0 < nwork; r0 += 2 * TP) {
+      const int i = r0 + 2 * threadIdx.y;
+      const int ra = listed ? (i < nwork ? ba.bc->upd_list[i] : ba.nrhs) : i;
+      const int rb = listed ? (i + 1 < nwork ? ba.bc->upd_list[i + 1] : ba.nrhs) : i + 1;
+      const bool act_a = site_ok && rhs_active(ba, ra);
+      const bool act_b = site_ok && rhs_active(ba, rb);
+      double red_a[NR], red_b[NR];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) red_a[k] = red_b[k] = 0.0;
+      if (act_a || act_b) {
+        const In ia = in.at(act_a ? ra : rb), ib = in.at(act_b ? rb : ra);
+        float2 acc2[24];
+        dslash_site_tile2<DAGGER>(ia, ib, lk2, threadIdx.x, nb, top, bot, unit_fwd, unit_bwd, acc2);
+        float acc[24];
+        if (act_a) {
+#pragma unroll
+          for (int k = 0; k < 24; ++k) acc[k] = acc2[k].x;
+          epi.at(ra)(h, acc, red_a);
+        }
+        if (act_b) {
+#pragma unroll
+          for (int k = 0; k < 24; ++k) acc[k] = acc2[k].y;
+          epi.at(rb)(h, acc, red_b);
+        }
+      }
+      if constexpr (Epi::NRED > 0) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            red_a[k] += __shfl_down_sync(0xffffffffu, red_a[k], o);
+            red_b[k] += __shfl_down_sync(0xffffffffu, red_b[k], o);
+          }
+        if (threadIdx.x == 0) {
+          if (ra < ba.nrhs)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) sred[ra * NR + k] += red_a[k];
+          if (rb < ba.nrhs)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) sred[rb * NR + k] += red_b[k];
+        }
+      }
+    }
+  }
+  if constexpr (Epi::NRED > 0) {
+    __syncthreads();
+    for (int i = tid; i < ba.nrhs * NR; i += 32 * TP) ba.partials[(size_t)i * gridDim.x + blockIdx.x] = sred[i];
+  }
+}
+
 // Per-system dslash over a batch: the single-system site kernel with
 // blockIdx.y naming the system (in mode 1, the y-th entry of the list of
 // systems due for an update; blocks past the list's end return at once).
@@ -243,7 +504,8 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
   for (int k = 0; k < NR; ++k) red[k] = 0.0;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
     R acc[24];
-    dslash_site<DAGGER, TFIX, R8, Epi::NRED == 0>(g, v, gauge, h, parity, acc);
+    if constexpr (UseAsync<In, R8>::value) dslash_site_async<DAGGER, TFIX>(g, v, gauge, h, parity, acc);
+    else dslash_site<DAGGER, TFIX, R8, Epi::NRED == 0>(g, v, gauge, h, parity, acc);
     e(h, acc, red);
   }
   if constexpr (Epi::NRED > 0) {
@@ -333,6 +595,8 @@ struct BatchLaunch {
   int grid;     // multi-RHS dslash blocks (tr = 0: blocks per system), inner precision
   int blas_gx;  // site-kernel blocks per right-hand side
   int grid64 = 0;    // FP64 dslash (dslash_rhs_kernel): blocks per system; 0 = grid
+  int pack = 0;      // 1: two systems per thread in FP32x2 registers (tr = 2, 4, 8
+                     // systems per chunk: tr / 2 thread rows), FP32 / 16-bit storage
 };
 
 // blocks per system of the FP64 per-system dslash: the single-system grid
@@ -372,6 +636,27 @@ void launch_dslash_mrhs(const Geom& g, const BatchLaunch& bl, const In& in, cons
     return;
   }
   const int tr = bl.tr;
+  if constexpr (sizeof(R) == 4) {
+    if (bl.pack) {
+      const size_t smem2 = tile_link_bytes2<R>() + (size_t)bl.nrhs * NR * sizeof(double);
+#define WD_MRHS2_CASE(TRV)                                                                                  \
+  case TRV:                                                                                                 \
+    if (dagger)                                                                                             \
+      launch_pdl(dslash_mrhs2_kernel<true, In, G, Epi, TRV / 2>, dim3(grid), dim3(32, TRV / 2), smem2, s, g, \
+                 in, gauge, parity, epi, ba);                                                               \
+    else                                                                                                    \
+      launch_pdl(dslash_mrhs2_kernel<false, In, G, Epi, TRV / 2>, dim3(grid), dim3(32, TRV / 2), smem2, s,   \
+                 g, in, gauge, parity, epi, ba);                                                            \
+    break;
+      switch (tr) {
+        WD_MRHS2_CASE(2)
+        WD_MRHS2_CASE(4)
+        WD_MRHS2_CASE(8)
+      }
+#undef WD_MRHS2_CASE
+      return;
+    }
+  }
 #define WD_MRHS_CASE(TRV)                                                                                   \
   case TRV:                                                                                                 \
     if (dagger)                                                                                             \

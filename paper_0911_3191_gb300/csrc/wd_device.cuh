@@ -462,7 +462,6 @@ __device__ __forceinline__ void su3_from8(const float (&p)[8], float (&u)[18]) {
   n2 += a3r * a3r;
   n2 += a3i * a3i;
   const float rn = rsqrtf(n2);  // 1/N
-  const float N = n2 * rn;
   float b12 = b1r * b1r;
   b12 += b1i * b1i;
   const float a1m = sqrtf(fmaxf(0.f, 1.f - n2));

@@ -157,6 +157,7 @@ struct Ctx {
   unsigned long long batch_hu, batch_hl;
   int batch_tr, batch_grid;  // tuned multi-RHS dslash shape for (batch_n, batch_prec);
                              // batch_tr 0: not tuned, -1: one system per block row
+  int batch_pack;            // 1: two systems per thread (FP32x2 registers)
   double* batch_host;     // pinned mirror of per-system results
   std::string last_error;
 };

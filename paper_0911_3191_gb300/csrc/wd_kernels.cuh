@@ -522,7 +522,7 @@ struct DslashOccupancy {
 
 // 16-bit spinors with 12-real links take the cp.async pipeline of
 // wd_async.cuh (neighbour words staged through shared memory)
-constexpr bool kAsync16 = false;
+constexpr bool kAsync16 = true;
 template <class In, bool R8>
 struct UseAsync {
   static constexpr bool value = kAsync16 && In::kBytesPerSite == 52 && !R8;

@@ -126,6 +126,7 @@ wd_status ensure_batch(wd_ctx* ctx, int n, int prec) {
   c.batch_n = n;
   c.batch_prec = prec;
   c.batch_tr = 0;
+  c.batch_pack = 0;
   return WD_OK;
 }
 
@@ -152,10 +153,14 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
       const size_t bar = line.find('|');
       if (bar != std::string::npos && line.substr(0, bar) == key) {
         std::istringstream v(line.substr(bar + 1));
-        int tr = 0, grid = 0;
-        if (v >> tr >> grid && (tr == 0 || tr == 1 || tr == 2 || tr == 4 || tr == 8) && grid > 0) {
+        int tr = 0, grid = 0, pack = 0;
+        const bool shape = static_cast<bool>(v >> tr >> grid);
+        if (shape && !(v >> pack)) pack = 0;  // entries without the layout field: one system per thread
+        if (shape && (tr == 0 || tr == 1 || tr == 2 || tr == 4 || tr == 8) && grid > 0 &&
+            (pack == 0 || (pack == 1 && tr >= 2 && prec != WD_F64))) {
           c.batch_tr = tr ? tr : -1;
           c.batch_grid = grid;
+          c.batch_pack = pack;
           return WD_OK;
         }
       }
@@ -170,17 +175,23 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
   WB_CK(ctx, cudaEventCreate(&e0));
   WB_CK(ctx, cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_tr = 4, best_grid = c.num_sms * 4;
-  // tr 0: one system per block row, 128 sites per block
-  const int trs[5] = {0, 1, 2, 4, 8};
+  int best_tr = 4, best_grid = c.num_sms * 4, best_pack = 0;
+  // block shapes and register layouts: tr 0 is one system per block row (128
+  // sites per block); tr 1..8 systems per 32-site link tile, one system per
+  // thread, or (pack) two systems per thread in FP32x2 registers, tr / 2
+  // thread rows
+  const int trs[8] = {0, 1, 2, 4, 8, 2, 4, 8};
+  const int packs[8] = {0, 0, 0, 0, 0, 1, 1, 1};
+  const int ncand = prec == WD_F64 ? 5 : 8;
   const int mults[4] = {2, 4, 8, 16};
   const int nblk128 = (c.g.Vh + kDslashBlock - 1) / kDslashBlock;
-  for (int ti = 0; ti < 5; ++ti) {
+  for (int ti = 0; ti < ncand; ++ti) {
     for (int mi = 0; mi < 4; ++mi) {
       int grid = c.num_sms * mults[mi];
       const int cap = trs[ti] ? ntiles : nblk128;
       if (grid > cap) grid = cap;
       bl.tr = trs[ti];
+      bl.pack = packs[ti];
       bl.grid = grid;
       o->dslash_batch(c, bl, b.tmp, b.r_hat, 1, 0, c.stream);  // warm-up
       WB_CK(ctx, cudaEventRecord(e0, c.stream));
@@ -193,6 +204,7 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
         best = ms;
         best_tr = trs[ti];
         best_grid = grid;
+        best_pack = packs[ti];
       }
     }
   }
@@ -201,9 +213,10 @@ wd_status tune_batch(wd_ctx* ctx, int n, int prec, BatchBufs& b) {
   WB_CK_LAUNCH(ctx);
   c.batch_tr = best_tr ? best_tr : -1;
   c.batch_grid = best_grid;
+  c.batch_pack = best_pack;
   if (cache) {
     std::ofstream f(cache, std::ios::app);
-    f << key << "|" << best_tr << " " << best_grid << "\n";
+    f << key << "|" << best_tr << " " << best_grid << " " << best_pack << "\n";
   }
   return WD_OK;
 }
@@ -214,6 +227,7 @@ BatchLaunch launch_shape(const Ctx& c, int n) {
                  blas_gx(c, n)};
   if (bl.tr && bl.grid > ntiles) bl.grid = ntiles;
   bl.grid64 = rhs_grid64(c.g, c.num_sms);
+  bl.pack = (c.batch_tr > 0) ? c.batch_pack : 0;
   return bl;
 }
 
@@ -426,6 +440,7 @@ void batch_release(Ctx& c) {
   c.batch_n = 0;
   c.batch_prec = -1;
   c.batch_tr = 0;
+  c.batch_pack = 0;
 }
 }  // namespace wd
 
@@ -444,6 +459,7 @@ wd_status wd_dslash_batch(wd_ctx* ctx, void* out, const void* in, int nrhs, wd_p
   if (c.batch_tr && c.batch_n == nrhs && c.batch_prec == prec) {
     bl.tr = std::max(c.batch_tr, 0);
     bl.grid = c.batch_grid;
+    bl.pack = c.batch_tr > 0 ? c.batch_pack : 0;
   }
   const int ntiles = (c.g.Vh + 31) / 32;
   if (bl.tr && bl.grid > ntiles) bl.grid = ntiles;

@@ -60,3 +60,15 @@ def test_reference_arm_json_contract(monkeypatch, capsys):
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_recorded_traffic_is_tied_to_the_kernel_sources(monkeypatch):
+    """The ncu traffic the bench line reports belongs to the kernel revision it
+    was captured on: with another source hash it is reported as null."""
+    key = ("q16", 12, "24x24x24x64", True)
+    monkeypatch.setattr(bench, "NCU_TRAFFIC_BYTES", {key: 1.0e8})
+    monkeypatch.setattr(bench, "KERNEL_SOURCES_SHA", bench.kernel_sources_sha())
+    assert bench.ncu_traffic(key) == 1.0e8
+    assert bench.ncu_traffic(("q16", 12, "64x64x64x128", True)) is None
+    monkeypatch.setattr(bench, "KERNEL_SOURCES_SHA", "0" * 16)
+    assert bench.ncu_traffic(key) is None

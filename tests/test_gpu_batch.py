@@ -138,7 +138,7 @@ def test_per_system_shape(tmp_path, monkeypatch, prec):
     cache = tmp_path / "tune.txt"
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    cache.write_text(f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} prec{prec} n{nrhs} sms{sms}|0 8\n")
+    cache.write_text(f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} prec{prec} n{nrhs} sms{sms} links12 tfix1|0 8\n")
     monkeypatch.setenv("WD_TUNE_CACHE", str(cache))
     wd = m.WilsonDirac(dims, t_antiperiodic=True)
     wd.load_gauge(U, temporal_gauge=True)
@@ -160,4 +160,50 @@ def test_per_system_shape(tmp_path, monkeypatch, prec):
         got = wd.download(fout[r * fb:(r + 1) * fb], prec, parity=m.ODD)
         want = oracle.dslash(s * parity_mask(dims, 0), U, dims, dagger=True, out_parity=1, tbc_anti=True)
         assert rel_err(got, want) <= TOL[prec], (prec, r)
-    assert "|0 8" in cache.read_text()
+    # the pinned entry was used: the tuner appended no line of its own
+    assert cache.read_text().count("\n") == 1 and "|0 8" in cache.read_text()
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3, 4])
+@pytest.mark.parametrize("tr", [2, 4, 8])
+def test_packed_pairs_shape(tmp_path, monkeypatch, prec, tr):
+    """Two systems per thread in FP32x2 registers (a tuning-cache entry with
+    the packed layout): the batched dslash for an odd number of systems (one
+    system of the last pair rides along unwritten) agrees with the oracle and
+    with the single-system kernel, and a batched solve reaches its tolerance
+    for every system."""
+    import torch
+
+    import paper_0911_3191_gb300 as m
+    dims = (8, 6, 4, 16)
+    U = li.gauge(dims, 0.5, 1013)
+    nrhs = 5
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} prec{prec} n{nrhs} sms{sms} links12 tfix0|{tr} 16 1\n")
+    monkeypatch.setenv("WD_TUNE_CACHE", str(cache))
+    wd = m.WilsonDirac(dims, t_antiperiodic=True)
+    wd.load_gauge(U)
+    srcs = [li.gaussian_spinor(dims, 5200 + r) for r in range(nrhs)]
+    kappas = [0.118, 0.12, 0.121, 0.123, 0.124]
+    xs = [np.zeros_like(b) for b in srcs]
+    infos = wd.solve_batch(xs, srcs, kappas, tol=1e-10, inner_precision=prec)
+    for x, b, k, info in zip(xs, srcs, kappas, infos):
+        rel = oracle.true_residual(x, b, U, dims, k, tbc_anti=True)
+        assert info.status == 0 and rel <= 1e-10, (prec, tr, k, info, rel)
+    fb = wd.field_bytes(prec)
+    fin = wd.new_field(prec, nrhs)
+    for r, s in enumerate(srcs):
+        wd.field_import(fin[r * fb:(r + 1) * fb], s, m.EVEN, prec)
+    single = wd.new_field(prec)
+    for dagger in (False, True):
+        fout = wd.new_field(prec, nrhs)
+        wd.dslash_batch(fout, fin, nrhs, m.ODD, dagger, prec)
+        for r, s in enumerate(srcs):
+            got = wd.download(fout[r * fb:(r + 1) * fb], prec, parity=m.ODD)
+            want = oracle.dslash(s * parity_mask(dims, 0), U, dims, dagger=dagger, out_parity=1, tbc_anti=True)
+            assert rel_err(got, want) <= TOL[prec], (prec, tr, r, dagger)
+            wd.dslash(single, fin[r * fb:(r + 1) * fb], m.ODD, dagger, prec)
+            assert rel_err(got, wd.download(single, prec, parity=m.ODD)) <= TOL[prec] * (1 if prec <= 1 else 0.2)
+    assert cache.read_text().count("\n") == 1 and f"|{tr} 16 1" in cache.read_text()
+    wd.close()
