@@ -679,11 +679,12 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     // setup: 3 norms, b_hat, zero x, control init, solver setup (4 kernels,
     // CG: 2 dslash + 2 zero); per iteration: BiCGstab 7 (CG 5) + loop control;
-    // per reliable update: BiCGstab 3 (CG 5); end: x_o with the odd residual,
+    // per reliable update: BiCGstab 4 (5 with a lower inner precision: the
+    // quantisation pass), CG 5; end: x_o with the odd residual,
     // and the even residual dslash
     const long long setup = 3 + 1 + 1 + 1 + 4;
     const long long per_it = (p.solver == WD_BICGSTAB ? 7 : 5) + (p.use_graph ? 1 : 0);
-    const long long per_up = (p.solver == WD_BICGSTAB) ? 4 : 5;
+    const long long per_up = (p.solver == WD_BICGSTAB) ? (p.inner_precision == WD_F64 ? 4 : 5) : 5;
     info->kernel_launches = setup + (long long)hc.iter * per_it + (long long)hc.updates * per_up + 2;
   }
   if (result != WD_OK) {

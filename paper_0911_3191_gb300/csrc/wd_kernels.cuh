@@ -500,6 +500,64 @@ struct EpiRelupBicg {
   }
 };
 
+// The FP64 part of the BiCGstab reliable update for an FP32 or 16-bit inner
+// precision: r = b_hat - (x + c acc) in FP64, stored rounded to FP32 (the
+// values EpiRelupBicg rounds before quantising); OpRelupQuant then finishes
+// the update in a bandwidth-bound pass, so the FP64-pipe-bound dslash carries
+// no FP32 epilogue work and no reductions.
+struct EpiResidF32 {
+  static constexpr int NRED = 0;
+  SpinorF32 out;
+  SpinorF64 b, x;
+  Coef c;
+  __device__ __forceinline__ void operator()(int h, double (&a)[24], double*) const {
+    double bv[24], xv[24];
+    b.load(h, bv);
+    x.load(h, xv);
+    const double cc = c.get();
+    float q[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) q[k] = (float)(bv[k] - (xv[k] + cc * a[k]));
+    out.store_f(h, q);
+  }
+};
+
+// r_hat = quantised r; reduce |r|^2 (from the FP32 values, one FP64 add per
+// site), <r_tilde, r_hat> and |r_hat|^2: the reductions of EpiRelupBicg
+template <class RH, class RT, class Fin>
+struct OpRelupQuant {
+  static constexpr int NRED = 4;
+  SpinorF32 r;
+  RH rh;
+  RT rt;
+  RedScratch rs;
+  Fin fin;
+  __device__ __forceinline__ void operator()(int h, double* red) const {
+    float q[24];
+    r.load(h, q);
+    float n = 0.f;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) n += q[k] * q[k];
+    red[0] += (double)n;
+    rh.store_get(h, q);
+    float wv[24];
+    rt.load(h, wv);
+    float re = 0.f, im = 0.f, m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re += wv[2 * k] * q[2 * k];
+      re += wv[2 * k + 1] * q[2 * k + 1];
+      im += wv[2 * k] * q[2 * k + 1];
+      im -= wv[2 * k + 1] * q[2 * k];
+      m += q[2 * k] * q[2 * k];
+      m += q[2 * k + 1] * q[2 * k + 1];
+    }
+    red[1] += (double)re;
+    red[2] += (double)im;
+    red[3] += (double)m;
+  }
+};
+
 // --------------------------------------------------------------- kernels
 // Programmatic dependent launch: the solver's kernels are launched with the
 // programmatic-serialization attribute, so a kernel's blocks are scheduled
@@ -1193,10 +1251,21 @@ struct Impl {
     accumulate(c, b, s);
     EpiStore<SpinorF64> e0{T64::view(b.tmp64, g)};
     launch_dslash<double>(c, T64::view(b.x, g), T64::gauge(c), 1, 0, e0, s);
-    EpiRelupBicg<S, S, FinRelupBicg> e1{T64::view(b.b_hat, g), T64::view(b.x, g), T::view(b.r_hat, g),
-                                         T::view(b.r_tilde, g), Coef{0.0, &b.ctl->neg_kappa2}, c.red,
-                                         FinRelupBicg{b.ctl}};
-    launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 0, e1, s);
+    if constexpr (P != WD_F64) {
+      // r in FP32 in the FP64 residual buffer (unused by BiCGstab), then the
+      // quantisation and reductions in a pass of their own
+      EpiResidF32 e1{TX::view(b.r, g), T64::view(b.b_hat, g), T64::view(b.x, g), Coef{0.0, &b.ctl->neg_kappa2}};
+      launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 0, e1, s);
+      launch_sites(c, g.Vh,
+                   OpRelupQuant<S, S, FinRelupBicg>{TX::view(b.r, g), T::view(b.r_hat, g), T::view(b.r_tilde, g),
+                                                    c.red, FinRelupBicg{b.ctl}},
+                   s);
+    } else {
+      EpiRelupBicg<S, S, FinRelupBicg> e1{T64::view(b.b_hat, g), T64::view(b.x, g), T::view(b.r_hat, g),
+                                           T::view(b.r_tilde, g), Coef{0.0, &b.ctl->neg_kappa2}, c.red,
+                                           FinRelupBicg{b.ctl}};
+      launch_dslash<double>(c, T64::view(b.tmp64, g), T64::gauge(c), 0, 0, e1, s);
+    }
     launch_sites(c, g.Vh, OpRestart<S>{T::view(b.r_tilde, g), T::view(b.r_hat, g), T::view(b.p, g), T::view(b.v, g),
                                        b.ctl},
                  s);
