@@ -15,7 +15,8 @@
 //
 // GB300 layout of the work: the multi-shift BiCGstab runs in FP32 storage
 // (two FP32 M_hat applications per iteration serve every kappa; per-shift
-// vectors x_k, p_k updated by one fused kernel over all shifts) down to a
+// vectors x_k, p_k updated by one fused kernel over all shifts; every scalar
+// on the device, the loop one CUDA graph) down to a
 // relative residual of 1e-7 (or the requested tol if larger); each kappa is
 // then finished by the mixed-precision reliable-update solver of Alg. 2 on its
 // FP64 residual (b - M x_k, x_k += correction), which brings the FP64 true
@@ -143,12 +144,147 @@ __device__ __forceinline__ void cmad4(float4& y, float2 c, float4 x) {
   y.w += c.y * x.z;
 }
 
+// Device state of one shifted-family BiCGstab: the seed's scalars, the
+// shifted recurrences (Jegerlehner's f, g and the product pi of the
+// (1 + omega tau) factors), and the per-shift update coefficients the
+// finaliser of each iteration writes for the fused update kernel.
+struct MsCtl {
+  double2 rho, alpha, omega;
+  double stop;       // tol_rel |source|
+  int iters, max_iter, done, failed, status, n, in_graph, loops;
+  unsigned long long h_loop;
+  double tau[kMaxShifts];
+  double2 fz[kMaxShifts], gz[kMaxShifts], pz[kMaxShifts];
+  int active[kMaxShifts];
+  ShiftCoefs cf;
+};
+
+__device__ __forceinline__ double2 c_conj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 c_scale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double c_abs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ float2 c_f2(double2 z) { return make_float2((float)z.x, (float)z.y); }
+__device__ __forceinline__ void ms_fail(MsCtl* m, int status) {
+  if (!m->failed) m->status = status;
+  m->failed = 1;
+  m->done = 1;
+}
+
+// setup: rho = <r_tilde, r> (t = {<r, r_tilde>, |r|^2}), the stop
+struct FinMsSetup {
+  MsCtl* m;
+  double tol_rel;
+  __device__ void operator()(const double* t) const {
+    m->rho = c_conj(make_double2(t[0], t[1]));
+    if (!isfinite(t[2]) || !cfinite(m->rho)) ms_fail(m, WD_ERR_NUMERIC);
+    m->stop = tol_rel * sqrt(t[2]);
+  }
+};
+
+// alpha = rho / <r_tilde, v>  (t = {<v, r_tilde>, |v|^2})
+struct FinMsAlpha {
+  MsCtl* m;
+  __device__ void operator()(const double* t) const {
+    if (m->failed) return;
+    const double2 rtv = c_conj(make_double2(t[0], t[1]));
+    if (!cfinite(rtv)) { ms_fail(m, WD_ERR_NUMERIC); return; }
+    if (c_abs(rtv) == 0.0 || c_abs(m->rho) == 0.0) { ms_fail(m, WD_ERR_BREAKDOWN); return; }
+    m->alpha = cdiv(m->rho, rtv);
+  }
+};
+
+// omega = <t, s> / <t, t>  (t = {<t, s>, |t|^2})
+struct FinMsOmega {
+  MsCtl* m;
+  __device__ void operator()(const double* t) const {
+    if (m->failed) return;
+    const double2 ts = make_double2(t[0], t[1]);
+    const double tt = t[2];
+    if (!cfinite(ts) || !isfinite(tt)) { ms_fail(m, WD_ERR_NUMERIC); return; }
+    if (tt == 0.0) { ms_fail(m, WD_ERR_BREAKDOWN); return; }
+    m->omega = c_scale(1.0 / tt, ts);
+    if (c_abs(m->omega) == 0.0) ms_fail(m, WD_ERR_BREAKDOWN);
+  }
+};
+
+// end of iteration (t = {<r_new, r_tilde>, |r_new|^2}): beta, the shifted
+// recurrences and update coefficients of every active shift, retirement of
+// converged shifts, the stop test of the seed
+struct FinMsIter {
+  MsCtl* m;
+  __device__ void operator()(const double* t) const {
+    if (m->failed) return;
+    m->iters += 1;
+    const double2 rho_new = c_conj(make_double2(t[0], t[1]));
+    const double rn = sqrt(t[2]);
+    if (!isfinite(rn) || !cfinite(rho_new)) { ms_fail(m, WD_ERR_NUMERIC); return; }
+    const double2 alpha = m->alpha, omega = m->omega;
+    const double2 beta = cmul(cdiv(alpha, omega), cdiv(rho_new, m->rho));
+    for (int k = 0; k < m->n; ++k) {
+      ShiftCoef q{};
+      if (m->active[k]) {
+        const double sg = m->tau[k];
+        const double2 fz = m->fz[k], gz = m->gz[k], pz = m->pz[k];
+        const double2 f_next = c_add(fz, cmul(c_scale(sg, alpha), gz));
+        const double2 alpha_s = cdiv(cmul(alpha, fz), f_next);
+        const double2 one_ws = c_add(make_double2(1.0, 0.0), c_scale(sg, omega));
+        const double2 omega_s = cdiv(omega, one_ws);
+        const double2 pi_next = cmul(pz, one_ws);
+        const double2 ratio = cdiv(fz, f_next);
+        const double2 beta_s = cmul(beta, cmul(ratio, ratio));
+        const double2 qq = cdiv(cmul(beta_s, omega_s), alpha_s);
+        const double2 pf = cmul(pz, f_next);
+        q.ax = c_f2(alpha_s);
+        q.as = c_f2(cdiv(omega_s, pf));
+        q.c1 = c_f2(cdiv(make_double2(1.0, 0.0), cmul(pi_next, f_next)));
+        q.c2 = c_f2(beta_s);
+        q.c3 = c_f2(cdiv(c_scale(-1.0, qq), cmul(pz, fz)));
+        q.c4 = c_f2(cdiv(qq, pf));
+        q.active = 1;
+        m->gz[k] = c_add(f_next, cmul(beta, gz));
+        m->fz[k] = f_next;
+        m->pz[k] = pi_next;
+      }
+      m->cf.k[k] = q;
+    }
+    // the seed (k = 0) drives the iteration and stays active
+    for (int k = 1; k < m->n; ++k)
+      if (m->active[k] && rn <= m->stop * c_abs(cmul(m->pz[k], m->fz[k]))) m->active[k] = 0;
+    m->rho = rho_new;
+    if (rn <= m->stop || m->iters >= m->max_iter) m->done = 1;
+  }
+};
+
+// (<a, b>, |a|^2) with the finaliser Fin
+template <class Fin>
+struct OpDotNormMs {
+  static constexpr int NRED = 3;
+  OpDotNormF32 d;
+  Fin fin;
+  RedScratch rs;
+  __device__ __forceinline__ void operator()(int h, double* red) const { d(h, red); }
+};
+
+// out = a - c b with c read from the control block (alpha or omega)
+struct OpSubScaledMs {
+  static constexpr int NRED = 0;
+  SpinorF32 out, a, b;
+  const double2* c;
+  const MsCtl* m;
+  __device__ __forceinline__ void operator()(int h, double*) const {
+    if (m->failed) return;
+    OpSubScaledF32{out, a, b, (float)c->x, (float)c->y}(h, nullptr);
+  }
+};
+
 // All shifts in one pass: per site and float4 chunk of the spinor the seed's
 // r, r_new and s are read once and every active shift's x_k, p_k updated
-// (fields of the shifts rs bytes apart).
-__global__ void __launch_bounds__(kBlasBlock) shift_update_kernel(int n, int nshift, SpinorF32 xs, SpinorF32 ps,
-                                                                  SpinorF32 r, SpinorF32 r_new, SpinorF32 s,
-                                                                  ShiftCoefs cf) {
+// (fields of the shifts rs bytes apart), with the coefficients the
+// finaliser wrote; then r <- r_new for the next iteration.
+__global__ void __launch_bounds__(kBlasBlock) shift_update_kernel(int n, SpinorF32 xs, SpinorF32 ps, SpinorF32 r,
+                                                                  SpinorF32 r_new, SpinorF32 s, const MsCtl* m) {
+  if (m->failed) return;
+  const int nshift = m->n;
   const int stride = r.stride;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
 #pragma unroll 1
@@ -156,7 +292,7 @@ __global__ void __launch_bounds__(kBlasBlock) shift_update_kernel(int n, int nsh
       const size_t o = (size_t)c * stride + h;
       const float4 rv = __ldg(r.p + o), nv = __ldg(r_new.p + o), sv = __ldg(s.p + o);
       for (int k = 0; k < nshift; ++k) {
-        const ShiftCoef q = cf.k[k];
+        const ShiftCoef q = m->cf.k[k];
         if (!q.active) continue;
         float4* xk = (float4*)((char*)xs.p + (size_t)k * xs.rs) + o;
         float4* pk = (float4*)((char*)ps.p + (size_t)k * ps.rs) + o;
@@ -172,8 +308,33 @@ __global__ void __launch_bounds__(kBlasBlock) shift_update_kernel(int n, int nsh
         cmad4(t, q.c1, nv);
         *pk = t;
       }
+      r.p[o] = nv;
     }
   }
+}
+
+// last node of the WHILE body: continue while not done; the body count is
+// bounded here on its own (max_iter + 16 executions)
+__global__ void ms_loop_control_kernel(MsCtl* m) {
+  m->loops += 1;
+  if (m->loops > m->max_iter + 16 && !m->done) ms_fail(m, WD_ERR_NOT_CONVERGED);
+  if (m->in_graph) cudaGraphSetConditional((cudaGraphConditionalHandle)m->h_loop, m->done ? 0u : 1u);
+}
+
+__global__ void ms_init_kernel(MsCtl* m, int n, const double* tau, int max_iter, unsigned long long h_loop) {
+  MsCtl c;
+  memset(&c, 0, sizeof(c));
+  c.n = n;
+  c.max_iter = max_iter;
+  c.status = WD_OK;
+  c.in_graph = 1;
+  c.h_loop = h_loop;
+  for (int k = 0; k < n; ++k) {
+    c.tau[k] = tau[k];
+    c.fz[k] = c.gz[k] = c.pz[k] = make_double2(1.0, 0.0);
+    c.active[k] = 1;
+  }
+  *m = c;
 }
 
 float2 f2(cplx z) { return make_float2((float)z.real(), (float)z.imag()); }
@@ -185,100 +346,116 @@ namespace {
 // FP32 work fields of one shifted family (even parity)
 struct Family {
   void *r, *rt, *s, *t, *v, *rn;
+  void* todd;  // odd FP32 temporary of M_hat
   void* xs;  // n solutions, fb apart
   void* ps;  // n directions, fb apart
 };
 
 // BiCGstab over the shifted family (B + tau_k) y_k = src, B = M_hat(kappa_s),
-// tau_0 = 0 (the seed).  Scalars on the host; one fused update of all x_k,
-// p_k per iteration.  Returns when the seed's iterated residual reaches
+// tau_0 = 0 (the seed), run on the device: every scalar of the iteration
+// lives in the control block m, written by the finalisers of the fused
+// reductions, and the loop is one CUDA graph (a WHILE node over the
+// iteration), so the host waits once per family instead of three times per
+// iteration.  Returns when the seed's iterated residual reaches
 // tol_rel |src| (the shifted systems, whose residuals are the seed's divided
 // by |pi_k f_k| >= 1 in practice, stop being updated once they reach it).
 wd_status family_solve(wd_ctx* ctx, const void* src, double kappa_s, const std::vector<double>& tau, int max_iter,
-                       double tol_rel, Family& f, size_t fb, int& iters, long long& launches) {
+                       double tol_rel, Family& f, size_t fb, MsCtl* m, double* tau_dev, int& iters,
+                       long long& launches) {
   Ctx& c = ctx->c;
   cudaStream_t st = c.stream;
   const Geom& g = c.g;
   const int n = (int)tau.size();
-  double* hp = c.host_pinned;
+  const PrecOps* o32 = prec_ops(WD_F32);
   auto V = [&](const void* p, size_t rs = 0) { return Tr<WD_F32>::view(p, g, rs); };
-  auto dotnorm = [&](const void* a, const void* b) {  // -> hp[16..18] = <a, b>, |a|^2
-    launch_sites(c, g.Vh, OpDotNormF32{V(a), V(b), c.red, FinStore{c.scalars + 16, 3}}, st);
-    ++launches;
-  };
-  auto fetch = [&]() -> wd_status {
-    MS_CK(cudaMemcpyAsync(hp + 16, c.scalars + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MS_CK(cudaStreamSynchronize(st));
-    return WD_OK;
-  };
+  double* hp = c.host_pinned;
   MS_CK(cudaMemcpyAsync(f.r, src, fb, cudaMemcpyDeviceToDevice, st));
   MS_CK(cudaMemcpyAsync(f.rt, src, fb, cudaMemcpyDeviceToDevice, st));
   for (int k = 0; k < n; ++k) MS_CK(cudaMemcpyAsync((char*)f.ps + k * fb, src, fb, cudaMemcpyDeviceToDevice, st));
   MS_CK(cudaMemsetAsync(f.xs, 0, n * fb, st));
-  dotnorm(f.r, f.rt);
-  MS_ST(fetch());
-  iters = 0;
-  const double src2 = hp[18];
-  if (!std::isfinite(src2)) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: source not finite");
-  if (src2 == 0.0) return WD_OK;  // y = 0
-  cplx rho = std::conj(cplx(hp[16], hp[17]));
-  std::vector<cplx> fz(n, 1.0), gz(n, 1.0), pz(n, 1.0);
-  std::vector<char> active(n, 1);
-  const double stop = tol_rel * std::sqrt(src2);
-  const int gx = std::min((g.Vh + kBlasBlock - 1) / kBlasBlock, c.num_sms * 8);
-  while (iters < max_iter) {
-    ++iters;
-    MS_ST(wd_apply_M(ctx, f.v, f.ps, kappa_s, WD_M_SCHUR_EVEN, 0, WD_F32));  // v = B p_0
-    launches += 2;
-    dotnorm(f.v, f.rt);
-    MS_ST(fetch());
-    const cplx rtv = std::conj(cplx(hp[16], hp[17]));
-    if (!std::isfinite(std::abs(rtv))) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: NaN/Inf");
-    if (std::abs(rtv) == 0.0 || std::abs(rho) == 0.0) return merr(ctx, WD_ERR_BREAKDOWN, "multi-shift: <r0, v> = 0");
-    const cplx alpha = rho / rtv;
-    launch_sites(c, g.Vh, OpSubScaledF32{V(f.s), V(f.r), V(f.v), (float)alpha.real(), (float)alpha.imag()}, st);
-    MS_ST(wd_apply_M(ctx, f.t, f.s, kappa_s, WD_M_SCHUR_EVEN, 0, WD_F32));  // t = B s
-    launches += 3;
-    dotnorm(f.t, f.s);
-    MS_ST(fetch());
-    const cplx ts(hp[16], hp[17]);
-    const double tt = hp[18];
-    if (!std::isfinite(tt)) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: NaN/Inf");
-    if (tt == 0.0) return merr(ctx, WD_ERR_BREAKDOWN, "multi-shift: <t, t> = 0");
-    const cplx omega = ts / tt;
-    if (std::abs(omega) == 0.0) return merr(ctx, WD_ERR_BREAKDOWN, "multi-shift: omega = 0");
-    launch_sites(c, g.Vh, OpSubScaledF32{V(f.rn), V(f.s), V(f.t), (float)omega.real(), (float)omega.imag()}, st);
-    ++launches;
-    dotnorm(f.rn, f.rt);
-    MS_ST(fetch());
-    const cplx rho_new = std::conj(cplx(hp[16], hp[17]));
-    const double rn = std::sqrt(hp[18]);
-    const cplx beta = (alpha / omega) * (rho_new / rho);
-    ShiftCoefs cf{};
-    for (int k = 0; k < n; ++k) {
-      if (!active[k]) continue;
-      const double sg = tau[k];
-      const cplx f_next = fz[k] + alpha * sg * gz[k];
-      const cplx alpha_s = alpha * fz[k] / f_next;
-      const cplx omega_s = omega / (1.0 + omega * sg);
-      const cplx pi_next = pz[k] * (1.0 + omega * sg);
-      const cplx beta_s = beta * (fz[k] / f_next) * (fz[k] / f_next);
-      const cplx q = beta_s * omega_s / alpha_s;
-      cf.k[k] = ShiftCoef{f2(alpha_s), f2(omega_s / (pz[k] * f_next)), f2(1.0 / (pi_next * f_next)), f2(beta_s),
-                          f2(-q / (pz[k] * fz[k])), f2(q / (pz[k] * f_next)), 1, 0};
-      gz[k] = f_next + beta * gz[k];
-      fz[k] = f_next;
-      pz[k] = pi_next;
+  MS_CK(cudaMemcpyAsync(tau_dev, tau.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+
+  // the loop as a graph: WHILE(!done) { iteration; loop control }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct GraphGuard {
+    cudaGraph_t& g;
+    cudaGraphExec_t& e;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
     }
-    shift_update_kernel<<<gx, kBlasBlock, 0, st>>>(g.Vh, n, V(f.xs, fb), V(f.ps, fb), V(f.r), V(f.rn), V(f.s), cf);
-    ++launches;
-    MS_CK(cudaGetLastError());
-    for (int k = 1; k < n; ++k)  // the seed (k = 0) drives the iteration and stays active
-      if (active[k] && rn <= stop * std::abs(pz[k] * fz[k])) active[k] = 0;
-    std::swap(f.r, f.rn);
-    rho = rho_new;
-    if (!std::isfinite(rn)) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: NaN/Inf");
-    if (rn <= stop) break;
+  } guard{graph, exec};
+  MS_CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle hl;
+  MS_CK(cudaGraphConditionalHandleCreate(&hl, graph, 1, cudaGraphCondAssignDefault));
+  ms_init_kernel<<<1, 1, 0, st>>>(m, n, tau_dev, max_iter, (unsigned long long)hl);
+  launch_sites(c, g.Vh, OpDotNormMs<FinMsSetup>{OpDotNormF32{V(f.r), V(f.rt), c.red, FinStore{nullptr, 0}},
+                                                FinMsSetup{m, tol_rel}, c.red},
+               st);
+  launches += 2;
+  // a zero source needs no iteration (y = 0); a non-finite one is refused
+  MS_CK(cudaMemcpyAsync(hp + 16, &m->stop, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MS_CK(cudaMemcpyAsync(hp + 17, &m->failed, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MS_CK(cudaStreamSynchronize(st));
+  iters = 0;
+  int failed0 = 0;
+  memcpy(&failed0, hp + 17, sizeof(int));
+  if (failed0) return merr(ctx, WD_ERR_NUMERIC, "multi-shift: source not finite");
+  if (hp[16] == 0.0) return WD_OK;
+
+  union Raw {  // zero-initialised node parameters (the type has no default constructor)
+    cudaGraphNodeParams p;
+    unsigned char bytes[sizeof(cudaGraphNodeParams)];
+    Raw() { memset(bytes, 0, sizeof(bytes)); }
+  } raw;
+  cudaGraphNodeParams& wp = raw.p;
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hl;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  MS_CK(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  MS_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t unused;
+  MS_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  {
+    const int gx = std::min((g.Vh + kBlasBlock - 1) / kBlasBlock, c.num_sms * 8);
+    auto apply_B = [&](void* out, const void* in) {  // out = M_hat(kappa_s) in
+      o32->dslash(c, f.todd, in, 1, 0, cs);
+      o32->dslash_xpay(c, out, f.todd, in, -kappa_s * kappa_s, nullptr, 0, 0, cs);
+    };
+    apply_B(f.v, f.ps);  // v = B p_0
+    launch_sites(c, g.Vh, OpDotNormMs<FinMsAlpha>{OpDotNormF32{V(f.v), V(f.rt), c.red, FinStore{nullptr, 0}},
+                                                  FinMsAlpha{m}, c.red},
+                 cs);
+    launch_sites(c, g.Vh, OpSubScaledMs{V(f.s), V(f.r), V(f.v), &m->alpha, m}, cs);  // s = r - alpha v
+    apply_B(f.t, f.s);                                                              // t = B s
+    launch_sites(c, g.Vh, OpDotNormMs<FinMsOmega>{OpDotNormF32{V(f.t), V(f.s), c.red, FinStore{nullptr, 0}},
+                                                  FinMsOmega{m}, c.red},
+                 cs);
+    launch_sites(c, g.Vh, OpSubScaledMs{V(f.rn), V(f.s), V(f.t), &m->omega, m}, cs);  // r_new = s - omega t
+    launch_sites(c, g.Vh, OpDotNormMs<FinMsIter>{OpDotNormF32{V(f.rn), V(f.rt), c.red, FinStore{nullptr, 0}},
+                                                 FinMsIter{m}, c.red},
+                 cs);
+    shift_update_kernel<<<gx, kBlasBlock, 0, cs>>>(g.Vh, V(f.xs, fb), V(f.ps, fb), V(f.r), V(f.rn), V(f.s), m);
+    ms_loop_control_kernel<<<1, 1, 0, cs>>>(m);
+  }
+  const cudaError_t ce = cudaStreamEndCapture(cs, &unused);
+  cudaStreamDestroy(cs);
+  MS_CK(ce);
+  MS_CK(cudaGraphInstantiate(&exec, graph, 0));
+  MS_CK(cudaGraphLaunch(exec, st));
+  MsCtl hm;
+  MS_CK(cudaMemcpyAsync(&hm, m, sizeof(MsCtl), cudaMemcpyDeviceToHost, st));
+  MS_CK(cudaStreamSynchronize(st));
+  iters = hm.iters;
+  launches += (long long)hm.loops * 11;
+  if (hm.failed) {
+    const char* what = hm.status == WD_ERR_BREAKDOWN ? "multi-shift: breakdown" : "multi-shift: NaN/Inf";
+    return merr(ctx, (wd_status)(hm.status ? hm.status : WD_ERR_NUMERIC), what);
   }
   return WD_OK;
 }
@@ -312,9 +489,12 @@ wd_status multishift_core(wd_ctx* ctx, int n, char* x, const char* b, const doub
   const size_t f64 = Tr<WD_F64>::bytes(g.stride), f32 = Tr<WD_F32>::bytes(g.stride);
   DevBuf mem;
   mem.s = st;
-  const size_t bytes64 = (size_t)(2 + 2 + 1) * f64, bytes32 = (size_t)(7 + 3 * n) * f32;
-  MS_CK(cudaMallocAsync(&mem.p, bytes64 + bytes32, st));
+  const size_t bytes64 = (size_t)(2 + 2 + 1) * f64, bytes32 = (size_t)(8 + 3 * n) * f32;
+  const size_t bytes_ctl = align256(sizeof(MsCtl)) + align256(kMaxShifts * sizeof(double));
+  MS_CK(cudaMallocAsync(&mem.p, bytes_ctl + bytes64 + bytes32, st));
   char* q = (char*)mem.p;
+  MsCtl* mctl = (MsCtl*)q;  q += align256(sizeof(MsCtl));
+  double* tau_dev = (double*)q; q += align256(kMaxShifts * sizeof(double));
   char* tfull = q;  q += 2 * f64;   // M x_k, then the correction e
   char* rfull = q;  q += 2 * f64;   // b - M x_k
   char* w64 = q;    q += f64;       // D_eo b_o, and a conversion scratch
@@ -325,6 +505,7 @@ wd_status multishift_core(wd_ctx* ctx, int n, char* x, const char* b, const doub
   fam.t = q;  q += f32;
   fam.v = q;  q += f32;
   fam.rn = q; q += f32;
+  fam.todd = q; q += f32;
   char* src32 = q; q += f32;
   char* ys = q; q += n * f32;
   char* zs = q; q += n * f32;
@@ -355,7 +536,7 @@ wd_status multishift_core(wd_ctx* ctx, int n, char* x, const char* b, const doub
   if (be2 > 0.0) {
     o32->from_f64(c, src32, b_e, st);
     fam.xs = ys;
-    MS_ST(family_solve(ctx, src32, ks, tau, params->max_iter, stage_tol, fam, f32, it_u, launches));
+    MS_ST(family_solve(ctx, src32, ks, tau, params->max_iter, stage_tol, fam, f32, mctl, tau_dev, it_u, launches));
   } else {
     MS_CK(cudaMemsetAsync(ys, 0, n * f32, st));
   }
@@ -364,7 +545,7 @@ wd_status multishift_core(wd_ctx* ctx, int n, char* x, const char* b, const doub
     o32->from_f64(c, src32, w64, st);
     launches += 2;
     fam.xs = zs;
-    MS_ST(family_solve(ctx, src32, ks, tau, params->max_iter, stage_tol, fam, f32, it_w, launches));
+    MS_ST(family_solve(ctx, src32, ks, tau, params->max_iter, stage_tol, fam, f32, mctl, tau_dev, it_w, launches));
   }
   const int ms_iters = it_u + it_w;
   wd_status worst = WD_OK;
