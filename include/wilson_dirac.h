@@ -66,7 +66,8 @@ typedef enum {
   WD_ERR_INVALID_ARG = 1, /* bad pointer, size, enum or dims                 */
   WD_ERR_OOM = 2,         /* device allocation failed                        */
   WD_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
-  WD_ERR_NOT_CONVERGED = 4, /* max_iter reached; x and info are still written */
+  WD_ERR_NOT_CONVERGED = 4, /* max_iter reached, or the reported FP64 true
+                               residual above tol; x and info are still written */
   WD_ERR_BREAKDOWN = 5,   /* Krylov breakdown (rho, <r0,v> or <t,t> = 0)      */
   WD_ERR_NUMERIC = 6,     /* NaN or Inf met in a reduction                    */
   WD_ERR_TIMEOUT = 7,     /* a bounded device wait gave up                    */
@@ -243,7 +244,12 @@ typedef struct {
  * solution x, the source and the true residual in FP64 (Sec. 5.3).
  * x, b: host FP64 fields in the host layout (V x 24 doubles).  On return x
  * holds the solution and *info is filled even when not converged (status
- * WD_ERR_NOT_CONVERGED / WD_ERR_BREAKDOWN / WD_ERR_NUMERIC). */
+ * WD_ERR_NOT_CONVERGED / WD_ERR_BREAKDOWN / WD_ERR_NUMERIC).  WD_OK means
+ * info->true_rel_residual, the full FP64 residual of the returned x, is at
+ * most tol; the device loop stops on the Schur residual of its last reliable
+ * update, and a returned x whose full residual is above tol gives
+ * WD_ERR_NOT_CONVERGED (the same rule holds for the batched solves and the
+ * server). */
 wd_status wd_solve(wd_ctx *ctx, double *x, const double *b, double kappa, const wd_solve_params *params,
                    wd_solve_info *info);
 

@@ -127,9 +127,8 @@ __device__ __forceinline__ void async_hop(const AsyncSlots& sm, const Geom& g, b
       sw[4 * c] = d.x; sw[4 * c + 1] = d.y; sw[4 * c + 2] = d.z; sw[4 * c + 3] = d.w;
     }
     float psi[24], hs[12];
-    In::words_biased(sw, psi);
-    if constexpr (In::kBias != 0.f) project_biased<MU, S>(psi, hs, In::kBias);
-    else project<MU, S>(psi, hs);
+    In::words(sw, psi);
+    project<MU, S>(psi, hs);
     float gs[12];
     su3_mul<!FWD>(u, hs, gs);
     reconstruct_scaled<MU, S>(gs, acc, w);

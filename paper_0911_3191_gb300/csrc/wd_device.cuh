@@ -98,7 +98,7 @@ constexpr float kInv32767 = 3.0518509475997192e-05f;  // (float)(1.0 / 32767.0)
 struct SpinorF64 {
   using real = double;
   static constexpr bool kScaled = false;
-  static constexpr float kBias = 0.f;
+  static constexpr bool kIntCodes = false;
   double2* p;
   int stride;
   size_t rs;  // bytes from one right-hand side's field to the next (batches)
@@ -143,7 +143,7 @@ struct SpinorF64 {
 struct SpinorF32 {
   using real = float;
   static constexpr bool kScaled = false;
-  static constexpr float kBias = 0.f;
+  static constexpr bool kIntCodes = false;
   float4* p;
   int stride;
   size_t rs;
@@ -221,11 +221,12 @@ struct Spinor16 {
     return v;
   }
 
-  // int16 code q -> float q exactly, on the integer and FP32 pipes: the
-  // offset-binary value q + 32768 is placed in the mantissa of 2^23 and the
-  // sum 2^23 + 2^15 subtracted (no int-to-float conversion instruction).
+  // int16 code q -> float q exactly, by the conversion unit: the 16-bit
+  // stencil is issue-bound on the integer and FP32 pipes and leaves that unit
+  // idle, and one conversion per code costs fewer instructions than decoding
+  // the code on the busy pipes
   static __device__ __forceinline__ float q16_to_float(uint32_t half_bits) {
-    return __uint_as_float(0x4B000000u | (half_bits ^ 0x8000u)) - 8421376.0f;
+    return __int2float_rn((int)(short)(half_bits & 0xffffu));
   }
   static __device__ __forceinline__ float lo(uint32_t w) {
     if constexpr (F == Fmt16::Q16) return q16_to_float(w & 0xffffu);
@@ -233,7 +234,7 @@ struct Spinor16 {
     else return __uint_as_float(w << 16);
   }
   static __device__ __forceinline__ float hi(uint32_t w) {
-    if constexpr (F == Fmt16::Q16) return q16_to_float(w >> 16);
+    if constexpr (F == Fmt16::Q16) return __int2float_rn(((int)w) >> 16);
     else if constexpr (F == Fmt16::H16) return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
     else return __uint_as_float(w & 0xffff0000u);
   }
@@ -242,37 +243,22 @@ struct Spinor16 {
     if constexpr (F == Fmt16::H16) {
       __half2 h = *reinterpret_cast<__half2*>(&w);
       return __half22float2(h);
-    } else if constexpr (F == Fmt16::Q16) {
-      // both codes to offset binary with one XOR, each placed under the
-      // exponent of 2^23 with one byte permute, then one subtraction each
-      const uint32_t x = w ^ 0x80008000u;
-      return make_float2(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)) - 8421376.0f,
-                         __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)) - 8421376.0f);
     } else {
       return make_float2(lo(w), hi(w));
     }
   }
-  // Q16 codes decoded without the final subtraction carry this offset
-  static constexpr float kBias = (F == Fmt16::Q16) ? 8421376.0f : 0.0f;
-  static __device__ __forceinline__ float2 pair_biased(uint32_t w) {
-    if constexpr (F == Fmt16::Q16) {
-      const uint32_t x = w ^ 0x80008000u;
-      return make_float2(__uint_as_float(__byte_perm(x, 0x4B000000u, 0x7610)),
-                         __uint_as_float(__byte_perm(x, 0x4B000000u, 0x7632)));
-    } else {
-      return pair(w);
-    }
-  }
+  // integer codes (Q16): the launch shapes of their kernels differ
+  static constexpr bool kIntCodes = (F == Fmt16::Q16);
   // the factor that turns raw values into field values, from the site norm
   static __device__ __forceinline__ float scale_of(float n) {
     if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);
     else return n;
   }
-  // 24 raw values from the 12 stored words, Q16 codes as q + kBias
-  static __device__ __forceinline__ void words_biased(const uint32_t (&w)[12], float (&v)[24]) {
+  // 24 raw values from the 12 stored words
+  static __device__ __forceinline__ void words(const uint32_t (&w)[12], float (&v)[24]) {
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
-      const float2 f = pair_biased(w[j]);
+      const float2 f = pair(w[j]);
       v[2 * j] = f.x;
       v[2 * j + 1] = f.y;
     }
@@ -285,17 +271,6 @@ struct Spinor16 {
       v[2 * j] = f.x;
       v[2 * j + 1] = f.y;
     }
-  }
-  // load_raw() with Q16 codes left as q + kBias (see project_biased)
-  __device__ __forceinline__ float load_raw_biased(int h, float (&v)[24]) const {
-    uint32_t w[12];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const uint4 d = __ldg(p + (size_t)c * stride + h);
-      w[4 * c] = d.x; w[4 * c + 1] = d.y; w[4 * c + 2] = d.z; w[4 * c + 3] = d.w;
-    }
-    words_biased(w, v);
-    return scale_of(__ldg(norm + h));
   }
   // raw 16-bit values as float (codes, or the normalised fp16/bf16 numbers)
   // plus the factor that turns them into field values
@@ -752,43 +727,6 @@ __device__ __forceinline__ void project(const R (&p)[24], R (&h)[12]) {
   }
 }
 
-// project() on values that all carry the offset B (Q16 codes decoded as
-// q + B, B = 2^23 + 2^15): a difference cancels B exactly; a sum is formed as
-// (a - 2B) + b, exact because both terms and the result are integers below
-// 2^24.  The results equal project() on the codes q, bit for bit, with one
-// add per projected value instead of three.
-template <int SG>
-__device__ __forceinline__ float pm_biased(float a, float b, float twoB) {
-  if constexpr (SG > 0) return __fadd_rn(__fsub_rn(a, twoB), b);
-  else return __fsub_rn(a, b);
-}
-template <int MU, int S_>
-__device__ __forceinline__ void project_biased(const float (&p)[24], float (&h)[12], float B) {
-  static_assert(MU < 3, "temporal hops are diagonal in this basis");
-  constexpr int S = (MU == 1) ? -S_ : S_;
-  const float twoB = 2.0f * B;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float p0r = p[(0 + c) * 2], p0i = p[(0 + c) * 2 + 1];
-    const float p1r = p[(3 + c) * 2], p1i = p[(3 + c) * 2 + 1];
-    const float p2r = p[(6 + c) * 2], p2i = p[(6 + c) * 2 + 1];
-    const float p3r = p[(9 + c) * 2], p3i = p[(9 + c) * 2 + 1];
-    float h0r, h0i, h1r, h1i;
-    if constexpr (MU == 0) {
-      h0r = pm_biased<-S>(p0r, p3i, twoB); h0i = pm_biased<S>(p0i, p3r, twoB);
-      h1r = pm_biased<-S>(p1r, p2i, twoB); h1i = pm_biased<S>(p1i, p2r, twoB);
-    } else if constexpr (MU == 1) {
-      h0r = pm_biased<-S>(p0r, p3r, twoB); h0i = pm_biased<-S>(p0i, p3i, twoB);
-      h1r = pm_biased<S>(p1r, p2r, twoB); h1i = pm_biased<S>(p1i, p2i, twoB);
-    } else {
-      h0r = pm_biased<-S>(p0r, p2i, twoB); h0i = pm_biased<S>(p0i, p2r, twoB);
-      h1r = pm_biased<S>(p1r, p3i, twoB); h1i = pm_biased<-S>(p1i, p3r, twoB);
-    }
-    h[c * 2] = h0r; h[c * 2 + 1] = h0i;
-    h[(3 + c) * 2] = h1r; h[(3 + c) * 2 + 1] = h1i;
-  }
-}
-
 template <int MU, int S_, typename R>
 __device__ __forceinline__ void reconstruct(const R (&g)[12], R (&a)[24]) {
   static_assert(MU < 3, "temporal hops are diagonal in this basis");
@@ -921,14 +859,9 @@ __device__ __forceinline__ void hop(const In& in, const G& gauge, int parity, in
   R psi[24];
   R w = 1;
   R hs[12];
-  if constexpr (In::kScaled && In::kBias != 0.f) {
-    w = in.load_raw_biased(h_nbr, psi);
-    project_biased<MU, S>(psi, hs, In::kBias);
-  } else {
-    if constexpr (In::kScaled) w = in.load_raw(h_nbr, psi);
-    else in.load(h_nbr, psi);
-    project<MU, S>(psi, hs);
-  }
+  if constexpr (In::kScaled) w = in.load_raw(h_nbr, psi);
+  else in.load(h_nbr, psi);
+  project<MU, S>(psi, hs);
   R u[18];
   gauge.template load_scaled<R8>(FWD ? parity : 1 - parity, MU, h_link, u, w);
   R gs[12];

@@ -572,9 +572,12 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // few more registers, and the FP64 kernel is bound by the FP64 pipe.
 template <typename R, class In, int NRED, bool TFIX, bool R8>
 struct DslashOccupancy {
+  // (the Q16 temporal-gauge store kernel spills at 5 blocks and runs 3 %
+  // faster at 4; the fp16 / bf16 ones are 1-2 % faster at 5)
   static constexpr int kMinBlocks = (sizeof(R) == 8)       ? 3
                                     : R8                  ? (NRED == 0 ? 4 : 3)
-                                    : In::kScaled         ? (TFIX ? (NRED == 0 ? 5 : 4) : (NRED == 0 ? 6 : 5))
+                                    : In::kScaled         ? (TFIX ? (NRED == 0 ? (In::kIntCodes ? 4 : 5) : 4)
+                                                                  : (NRED == 0 ? 6 : 5))
                                                           : (NRED == 0 ? 5 : 4);
 };
 
@@ -1127,7 +1130,7 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
     // SM for the small lattices.  The FP64 kernel (FP64-pipe bound; 6 %
     // slower at 24^3x64) and the general-link Q16 kernel (6 % slower at
     // 64^3x128) keep 16 blocks per SM.
-    constexpr bool kWave = !(sizeof(R) == 8 || (In::kScaled && In::kBias != 0.f && !kTfix));
+    constexpr bool kWave = !(sizeof(R) == 8 || (In::kIntCodes && !kTfix));
     static const int per_sm = kWave ? resident_blocks(k, kDslashBlock) : 16;
     const int grid = wave_grid(c.g.Vh, kDslashBlock, c.num_sms, per_sm);
     launch_pdl(k, dim3(grid), dim3(kDslashBlock), 0, s, c.g, in, gauge, parity, epi);

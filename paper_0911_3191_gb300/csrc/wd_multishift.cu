@@ -321,20 +321,25 @@ __global__ void ms_loop_control_kernel(MsCtl* m) {
   if (m->in_graph) cudaGraphSetConditional((cudaGraphConditionalHandle)m->h_loop, m->done ? 0u : 1u);
 }
 
+// one block: the control block is zeroed word by word in place (a local
+// copy of it would live on the stack), then its fields are set
 __global__ void ms_init_kernel(MsCtl* m, int n, const double* tau, int max_iter, unsigned long long h_loop) {
-  MsCtl c;
-  memset(&c, 0, sizeof(c));
-  c.n = n;
-  c.max_iter = max_iter;
-  c.status = WD_OK;
-  c.in_graph = 1;
-  c.h_loop = h_loop;
-  for (int k = 0; k < n; ++k) {
-    c.tau[k] = tau[k];
-    c.fz[k] = c.gz[k] = c.pz[k] = make_double2(1.0, 0.0);
-    c.active[k] = 1;
+  static_assert(sizeof(MsCtl) % sizeof(unsigned) == 0, "MsCtl is a whole number of words");
+  unsigned* w = reinterpret_cast<unsigned*>(m);
+  for (int i = threadIdx.x; i < (int)(sizeof(MsCtl) / sizeof(unsigned)); i += blockDim.x) w[i] = 0u;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    m->tau[k] = tau[k];
+    m->fz[k] = m->gz[k] = m->pz[k] = make_double2(1.0, 0.0);
+    m->active[k] = 1;
   }
-  *m = c;
+  if (threadIdx.x == 0) {
+    m->n = n;
+    m->max_iter = max_iter;
+    m->status = WD_OK;
+    m->in_graph = 1;
+    m->h_loop = h_loop;
+  }
 }
 
 float2 f2(cplx z) { return make_float2((float)z.real(), (float)z.imag()); }
@@ -389,7 +394,7 @@ wd_status family_solve(wd_ctx* ctx, const void* src, double kappa_s, const std::
   MS_CK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle hl;
   MS_CK(cudaGraphConditionalHandleCreate(&hl, graph, 1, cudaGraphCondAssignDefault));
-  ms_init_kernel<<<1, 1, 0, st>>>(m, n, tau_dev, max_iter, (unsigned long long)hl);
+  ms_init_kernel<<<1, 128, 0, st>>>(m, n, tau_dev, max_iter, (unsigned long long)hl);
   launch_sites(c, g.Vh, OpDotNormMs<FinMsSetup>{OpDotNormF32{V(f.r), V(f.rt), c.red, FinStore{nullptr, 0}},
                                                 FinMsSetup{m, tol_rel}, c.red},
                st);

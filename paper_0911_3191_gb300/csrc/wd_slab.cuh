@@ -33,7 +33,6 @@ inline int face_stride(const Geom& g) { return (g.XhYZ + 31) / 32 * 32; }
 struct FaceF64 {
   using real = double;
   static constexpr bool kScaled = false;
-  static constexpr float kBias = 0.f;
   const double2* p;
   int stride;
   template <typename R>
@@ -50,7 +49,6 @@ struct FaceF64 {
 struct FaceF32 {
   using real = float;
   static constexpr bool kScaled = false;
-  static constexpr float kBias = 0.f;
   const float4* p;
   int stride;
   template <typename R>
@@ -70,7 +68,6 @@ template <Fmt16 F>
 struct Face16 {
   using real = float;
   static constexpr bool kScaled = true;
-  static constexpr float kBias = 0.f;
   const uint4* a;
   const uint2* b;
   const float* norm;
