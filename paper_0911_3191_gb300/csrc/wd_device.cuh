@@ -309,22 +309,16 @@ struct Spinor16 {
   template <typename R>
   __device__ __forceinline__ void load(int h, R (&v)[24]) const {
     float f[24];
-    float s = load_raw(h, f);
+    const float s = load_raw(h, f);
+    const float2 ss = make_float2(s, s);
 #pragma unroll
-    for (int k = 0; k < 24; ++k) v[k] = (R)__fmul_rn(f[k], s);
-  }
-
-  static __device__ __forceinline__ uint32_t enc(float w, float scale) {
-    if constexpr (F == Fmt16::Q16) {
-      float q = rintf(__fmul_rn(w, scale));
-      q = fminf(fmaxf(q, -32767.f), 32767.f);
-      return (uint32_t)(uint16_t)(int16_t)q;
-    } else if constexpr (F == Fmt16::H16) {
-      return (uint32_t)__half_as_ushort(__float2half_rn(__fmul_rn(w, scale)));
-    } else {
-      return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(__fmul_rn(w, scale)));
+    for (int k = 0; k < 12; ++k) {
+      const float2 q = __fmul2_rn(make_float2(f[2 * k], f[2 * k + 1]), ss);
+      v[2 * k] = (R)q.x;
+      v[2 * k + 1] = (R)q.y;
     }
   }
+
   static __device__ __forceinline__ float f32(double d) { return __double2float_rn(d); }
   static __device__ __forceinline__ float f32(float f) { return f; }
 
@@ -348,32 +342,51 @@ struct Spinor16 {
       // |fl(f * scale)| <= 32767 (1 + 2^-24)^2 < 2^22 (so no clamp is needed
       // either: m is the largest |f|); the low 16 bits of s are then q in two's
       // complement, and s - 1.5 * 2^23 = q exactly
+      // (both values of a word by one packed multiply and one packed add)
       constexpr float kMagic = 12582912.0f;
-      float sv[24];
+      const float2 sc = make_float2(scale, scale), mg = make_float2(kMagic, kMagic);
+      float2 sv[12];
 #pragma unroll
-      for (int k = 0; k < 24; ++k) sv[k] = __fadd_rn(__fmul_rn(f[k], scale), kMagic);
+      for (int k = 0; k < 12; ++k) sv[k] = __fadd2_rn(__fmul2_rn(make_float2(f[2 * k], f[2 * k + 1]), sc), mg);
       uint32_t w[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) w[k] = __byte_perm(__float_as_uint(sv[2 * k]), __float_as_uint(sv[2 * k + 1]), 0x5410);
+      for (int k = 0; k < 12; ++k) w[k] = __byte_perm(__float_as_uint(sv[k].x), __float_as_uint(sv[k].y), 0x5410);
 #pragma unroll
       for (int c = 0; c < 3; ++c) p[(size_t)c * stride + h] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
       norm[h] = m;
       const float d = __fmul_rn(m, kInv32767);
+      const float2 dd = make_float2(d, d), nmg = make_float2(-kMagic, -kMagic);
 #pragma unroll
-      for (int k = 0; k < 24; ++k) v[k] = (R)__fmul_rn(__fsub_rn(sv[k], kMagic), d);
+      for (int k = 0; k < 12; ++k) {
+        const float2 q = __fmul2_rn(__fadd2_rn(sv[k], nmg), dd);
+        v[2 * k] = (R)q.x;
+        v[2 * k + 1] = (R)q.y;
+      }
       return;
     }
+    // fp16 / bf16: both values of a word scaled by one packed multiply and
+    // rounded (to nearest, ties to even, each) by one packing conversion
     uint32_t w[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) w[k] = enc(f[2 * k], scale) | (enc(f[2 * k + 1], scale) << 16);
+    for (int k = 0; k < 12; ++k) {
+      const float2 t = __fmul2_rn(make_float2(f[2 * k], f[2 * k + 1]), make_float2(scale, scale));
+      if constexpr (F == Fmt16::H16) {
+        const __half2 q = __floats2half2_rn(t.x, t.y);
+        w[k] = *reinterpret_cast<const uint32_t*>(&q);
+      } else {
+        const __nv_bfloat162 q = __floats2bfloat162_rn(t.x, t.y);
+        w[k] = *reinterpret_cast<const uint32_t*>(&q);
+      }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[(size_t)c * stride + h] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
     norm[h] = m;
-    float d = (F == Fmt16::Q16) ? __fmul_rn(m, kInv32767) : m;
+    const float2 dd = make_float2(m, m);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      v[2 * k] = (R)__fmul_rn(lo(w[k]), d);
-      v[2 * k + 1] = (R)__fmul_rn(hi(w[k]), d);
+      const float2 q = __fmul2_rn(pair(w[k]), dd);
+      v[2 * k] = (R)q.x;
+      v[2 * k + 1] = (R)q.y;
     }
   }
   template <typename R>
@@ -905,6 +918,9 @@ __device__ __forceinline__ void reconstruct_lower(const R (&g)[12], R (&a)[24]) 
   }
 }
 
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // The forward and backward hops of one spatial direction together, for
 // unscaled fields (FP64, FP32).  With X = U_mu(x) P_f psi(x + mu) and
 // B = U_mu^dag(x - mu) P_b psi(x - mu) (P_b the projector of opposite sign),
@@ -952,8 +968,11 @@ __device__ __forceinline__ void hop_pair(const In& in, const G& gauge, int parit
         acc[k] += re;
         acc[k + 1] += im;
       }
-      xd[k] = (R)2 * xd[k] - re;
-      xd[k + 1] = (R)2 * xd[k + 1] - im;
+      // one explicit FMA each: written as 2 x - y, the compiler turns 2 x
+      // into x + x and the FMA into two adds (on GB300's FP64 pipe, 12 more
+      // instructions per direction)
+      xd[k] = fma_rn((R)2, xd[k], -re);
+      xd[k + 1] = fma_rn((R)2, xd[k + 1], -im);
     }
   }
   reconstruct_lower<MU, SF, FIRST>(xd, acc);
