@@ -214,7 +214,7 @@ def cpu_baseline(U, b, dims, kappa, iters_full: int, sample_iters: int):
     dt = time.perf_counter() - t0
     per_solve = dt / sample_iters * iters_full
     return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
-            "kind": "oracle", "sample_iterations": sample_iters, "sample_seconds": round(dt, 3),
+            "kind": "oracle", "sample_iterations": sample_iters, "sample_seconds": round(dt, 6),
             "full_solve_iterations": iters_full, "scale": round(iters_full / sample_iters, 4),
             "extrapolated": True,
             "sample": f"{sample_iters} FP64 BiCGstab iterations of the {dims[0]}^3x{dims[3]} Schur solve "
@@ -258,7 +258,7 @@ def run_reference(args):
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(args, ws),
-            "cpu_baseline": {**vals[0], "value": v, "sample_seconds": round(step_s, 3)},
+            "cpu_baseline": {**vals[0], "value": v, "sample_seconds": round(step_s, 6)},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0

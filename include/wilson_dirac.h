@@ -297,8 +297,9 @@ wd_status wd_solve_batch(wd_ctx *ctx, int n, double *const *x, const double *con
  * sources b_e + kappa_k D_eo b_o are combinations of b_e and D_eo b_o, each
  * solved for all shifts at once (a second family only when b_o != 0).  The
  * multi-shift BiCGstab runs in FP32 storage to a relative residual of 1e-7
- * (or tol if larger); each kappa is then finished on its FP64 residual by the
- * solver of wd_solve (params->inner_precision, Alg. 2) to the FP64 true
+ * (or tol if larger); each kappa is then finished by the solver of wd_solve
+ * (params->inner_precision, Alg. 2) started from the multi-shift solution
+ * (its first step the FP64 Schur residual of that solution) to the FP64 true
  * residual tol.  params->solver is not used (the refinement is BiCGstab).
  * x[k]: host FP64 fields in the host layout (V x 24 doubles), written; b:
  * host FP64 source; kappas: host array.  infos[k].iters counts the shared

@@ -58,6 +58,12 @@ __global__ void init_ctl_kernel(SolverCtl* ctl, double tol, double delta, int ma
   *ctl = c;
 }
 
+// an initial guess that meets the tolerance: no iteration
+__global__ void mark_done_kernel(SolverCtl* ctl) {
+  ctl->status = WD_OK;
+  ctl->done = 1;
+}
+
 // ---- gauge field: host layout -> even-odd structure of arrays (S1)
 __global__ void gauge_pack_f64_kernel(Geom g, const double* lex, double2* out, int nc) {
   const int n = 2 * g.Vh;
@@ -554,7 +560,7 @@ wd_status build_graph(wd_ctx* ctx, int solver, int prec, unsigned long long* h_u
 }
 
 wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kappa, const wd_solve_params* prm,
-                       wd_solve_info* info) {
+                       wd_solve_info* info, bool x0 = false) {
   Ctx& c = ctx->c;
   const auto t0 = std::chrono::steady_clock::now();
   wd_solve_params p{1e-10, 0.1, 10000, WD_BICGSTAB, WD_F64, 1, 0, 0};
@@ -564,6 +570,8 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   if (p.restart && p.inner_precision == WD_F64)
     return set_err(ctx, WD_ERR_INVALID_ARG, "defect correction needs a lower inner precision");
   if (p.solver != WD_BICGSTAB && p.solver != WD_CGNR) return set_err(ctx, WD_ERR_INVALID_ARG, "bad solver");
+  if (x0 && (p.solver != WD_BICGSTAB || p.restart))
+    return set_err(ctx, WD_ERR_INVALID_ARG, "an initial guess needs BiCGstab with reliable updates");
   if (!(p.tol > 0.0) || p.max_iter <= 0) return set_err(ctx, WD_ERR_INVALID_ARG, "bad tol or max_iter");
   if (p.inner_precision == WD_F64) p.delta = 0.0;  // pure FP64: update only to confirm convergence
   else if (!(p.delta > 0.0 && p.delta < 1.0)) return set_err(ctx, WD_ERR_INVALID_ARG, "delta must be in (0,1)");
@@ -587,7 +595,23 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   o64->norm2(c, c.scalars + 1, b_o, s);
   o64->dslash_xpay(c, sb.b_hat, b_o, b_e, kappa, nullptr, 0, 0, s);
   o64->norm2(c, c.scalars + 2, sb.b_hat, s);
-  o64->zero(c, sb.x, s);
+  const void* setup_src = sb.b_hat;
+  if (x0) {
+    // start from x0_e: the accumulator holds it and the iteration starts from
+    // r0 = b_hat - M_hat x0_e in FP64 (tmp64 = D_oe x0_e, then the even rows),
+    // kept in the FP64 residual buffer, which BiCGstab does not use otherwise
+    using T64 = Tr<WD_F64>;
+    WD_CK(ctx, cudaMemcpyAsync(sb.x, x_e, f64, cudaMemcpyDeviceToDevice, s));
+    EpiStore<SpinorF64> e0{T64::view(sb.tmp64, c.g)};
+    launch_dslash<double>(c, T64::view(sb.x, c.g), T64::gauge(c), 1, 0, e0, s);
+    EpiResid<SpinorF64, SpinorF64, SpinorF64, FinStore> e1{T64::view(sb.r, c.g), true, T64::view(sb.b_hat, c.g),
+                                                           T64::view(sb.x, c.g), Coef{-kappa * kappa, nullptr},
+                                                           c.red, FinStore{c.scalars + 6, 1}};
+    launch_dslash<double>(c, T64::view(sb.tmp64, c.g), T64::gauge(c), 0, 0, e1, s);
+    setup_src = sb.r;
+  } else {
+    o64->zero(c, sb.x, s);
+  }
   WD_CK_LAUNCH(ctx, "solve setup");
 
   unsigned long long hu = 0, hl = 0;
@@ -602,14 +626,16 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   }
   init_ctl_kernel<<<1, 1, 0, s>>>(sb.ctl, p.tol, p.delta, p.max_iter, kappa, c.scalars, p.use_graph ? 1 : 0, hu,
                                   hl, p.restart ? 1 : 0);
-  if (p.solver == WD_BICGSTAB) oin->bicg_setup(c, sb, s);
+  if (p.solver == WD_BICGSTAB) oin->bicg_setup(c, sb, setup_src, s);
   else oin->cg_setup(c, sb, s);
   WD_CK_LAUNCH(ctx, "solver setup");
 
-  // a zero source needs no iteration
-  WD_CK(ctx, cudaMemcpyAsync(c.host_pinned, c.scalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // a zero source needs no iteration, nor does an initial guess that already
+  // meets the tolerance
+  WD_CK(ctx, cudaMemcpyAsync(c.host_pinned, c.scalars, 7 * sizeof(double), cudaMemcpyDeviceToHost, s));
   WD_CK(ctx, cudaStreamSynchronize(s));
   const double b2 = c.host_pinned[0] + c.host_pinned[1];
+  const bool start_converged = x0 && c.host_pinned[6] <= p.tol * p.tol * b2;
   SolverCtl hc;
   if (!(b2 > 0.0)) {
     o64->zero(c, x_e, s);
@@ -622,7 +648,9 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     return std::isfinite(b2) ? WD_OK : set_err(ctx, WD_ERR_NUMERIC, "source is not finite");
   }
 
-  if (p.use_graph) {
+  if (start_converged) {
+    mark_done_kernel<<<1, 1, 0, s>>>(sb.ctl);
+  } else if (p.use_graph) {
     WD_CK(ctx, cudaGraphLaunch(c.graph_exec, s));
   } else {
     for (;;) {
@@ -682,7 +710,9 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     // per reliable update: BiCGstab 4 (5 with a lower inner precision: the
     // quantisation pass), CG 5; end: x_o with the odd residual,
     // and the even residual dslash
-    const long long setup = 3 + 1 + 1 + 1 + 4;
+    // (an initial guess: its two residual dslashes instead of the zeroing,
+    // and the control update when it already meets the tolerance)
+    const long long setup = 3 + 1 + (x0 ? 2 : 1) + 1 + 4 + (start_converged ? 1 : 0);
     const long long per_it = (p.solver == WD_BICGSTAB ? 7 : 5) + (p.use_graph ? 1 : 0);
     const long long per_up = (p.solver == WD_BICGSTAB) ? (p.inner_precision == WD_F64 ? 4 : 5) : 5;
     info->kernel_launches = setup + (long long)hc.iter * per_it + (long long)hc.updates * per_up + 2;
@@ -744,6 +774,12 @@ wd_status wd_internal_import_full(wd_ctx* ctx, void* even, void* odd, const doub
   o->import_lex(c, odd, c.lex_staging, 1, c.stream);
   WD_CK_LAUNCH(ctx, "import");
   return WD_OK;
+}
+
+wd_status wd_internal_solve_x0(wd_ctx* ctx, void* x_full, const void* b_full, double kappa,
+                               const wd_solve_params* params, wd_solve_info* info) {
+  if (!ctx || !x_full || !b_full || x_full == b_full) return WD_ERR_INVALID_ARG;
+  return solve_device(ctx, x_full, b_full, kappa, params, info, true);
 }
 
 wd_status wd_internal_ensure_gauge(wd_ctx* ctx, int prec) {

@@ -53,6 +53,7 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 constexpr int kAsyncBlock = 128;  // threads per block of the kernels that use these slots
+constexpr bool kSpinPairs = true;  // packed FP32 pairs over spin rows (async_hop_pairs)
 constexpr int kAsyncStages = 3;
 
 struct AsyncSlots {
@@ -157,6 +158,188 @@ __device__ __forceinline__ void async_hop(const AsyncSlots& sm, const Geom& g, b
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same hops on spin pairs, with the packed FP32 operations of the sm_100
+// family (FFMA2, FMUL2: two lanes per instruction).  Every link element
+// multiplies two spin rows of the projected half spinor, so a packed operation
+// takes one element in both lanes and the pair (row 0, row 1).  The
+// accumulator holds pairs over spins (0, 1) and (3, 2); with that order every
+// reconstruction adds pair to pair except the lower rows of the z hop.  Each
+// value is computed by the operations of the scalar path, in its order and
+// with the same roundings (projections by +-1 multipliers are exact), so the
+// results are those of dslash_site.
+// acc2[c * 2 + ri] = (spin 0, spin 1), acc2[6 + c * 2 + ri] = (spin 3, spin 2)
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// g = U h (DAG false) or U^dag h (DAG true) on spin pairs: hr[j], hi[j] are
+// the real and imaginary parts of colour j of the two rows
+template <bool DAG>
+__device__ __forceinline__ void su3_mul_pairs(const float (&u)[18], const float2 (&hr)[3], const float2 (&hi)[3],
+                                              float2 (&gr)[3], float2 (&gi)[3]) {
+  float2 nh[3];  // -hi for U h, -hr for U^dag h
+#pragma unroll
+  for (int j = 0; j < 3; ++j) nh[j] = __fmul2_rn(DAG ? hr[j] : hi[j], dup2(-1.f));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int e = DAG ? (j * 3 + i) : (i * 3 + j);
+      const float2 ur = dup2(u[2 * e]), ui = dup2(u[2 * e + 1]);
+      if (j == 0) {  // + 0, as the scalar path's first term (a zero sum is +0)
+        gr[i] = __ffma2_rn(ur, hr[0], dup2(0.f));
+        gi[i] = __ffma2_rn(ur, hi[0], dup2(0.f));
+      } else {
+        gr[i] = __ffma2_rn(ur, hr[j], gr[i]);
+        gi[i] = __ffma2_rn(ur, hi[j], gi[i]);
+      }
+      if constexpr (DAG) {  // conj(U_ji) h_j
+        gr[i] = __ffma2_rn(ui, hi[j], gr[i]);
+        gi[i] = __ffma2_rn(ui, nh[j], gi[i]);
+      } else {  // U_ij h_j
+        gr[i] = __ffma2_rn(ui, nh[j], gr[i]);
+        gi[i] = __ffma2_rn(ui, hr[j], gi[i]);
+      }
+    }
+  }
+}
+
+// reconstruct_scaled() on spin pairs
+template <int MU, int S_>
+__device__ __forceinline__ void reconstruct_pairs(const float2 (&gr)[3], const float2 (&gi)[3], float2 (&a)[12],
+                                                  float w) {
+  constexpr int S = (MU == 1) ? -S_ : S_;
+  const float ws = w * (float)S;
+  const float2 wp = dup2(w);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a[2 * c] = __ffma2_rn(wp, gr[c], a[2 * c]);
+    a[2 * c + 1] = __ffma2_rn(wp, gi[c], a[2 * c + 1]);
+    float2& lr = a[6 + 2 * c];
+    float2& li = a[6 + 2 * c + 1];
+    if constexpr (MU == 0) {  // spin 3 += -S i g0, spin 2 += -S i g1
+      lr = __ffma2_rn(dup2(ws), gi[c], lr);
+      li = __ffma2_rn(dup2(-ws), gr[c], li);
+    } else if constexpr (MU == 1) {  // spin 3 += -S g0, spin 2 += S g1
+      lr = __ffma2_rn(make_float2(-ws, ws), gr[c], lr);
+      li = __ffma2_rn(make_float2(-ws, ws), gi[c], li);
+    } else {  // spin 3 += S i g1, spin 2 += -S i g0: crosses the pair
+      lr.x = fmaf(-ws, gi[c].y, lr.x);
+      lr.y = fmaf(ws, gi[c].x, lr.y);
+      li.x = fmaf(ws, gr[c].y, li.x);
+      li.y = fmaf(-ws, gr[c].x, li.y);
+    }
+  }
+}
+
+template <int K, bool DAGGER, bool TFIX, class In, class G>
+__device__ __forceinline__ void async_hop_pairs(const AsyncSlots& sm, const Geom& g, bool top, bool bot,
+                                                float2 (&acc)[12]) {
+  using H = HopK<K>;
+  constexpr int MU = H::MU;
+  constexpr bool FWD = H::FWD;
+  constexpr int S = (FWD != DAGGER) ? -1 : +1;
+  const int tid = threadIdx.x;
+  float w = In::scale_of(sm.sn[H::ST][tid]);
+  const bool unit = TFIX && MU == 3 && (FWD ? !top : !bot);
+  float u[18];
+  if (!unit) {
+    const uint4 a = sm.l4[H::ST][tid];
+    const uint2 b = sm.l2[H::ST][tid];
+    const uint32_t lw[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    G::from_words(lw, u);
+    if constexpr (G::kScaled) w *= G::kScale;  // Q16 links come back as raw codes
+  }
+  float2 hr[3], hi[3];
+  if constexpr (MU < 3) {
+    uint32_t sw[12];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint4 d = sm.sp[H::ST][c][tid];
+      sw[4 * c] = d.x; sw[4 * c + 1] = d.y; sw[4 * c + 2] = d.z; sw[4 * c + 3] = d.w;
+    }
+    // project() on pairs: p = (spin 0, spin 1) and q = (spin 3, spin 2), or
+    // (spin 2, spin 3) for z; word s * 3 + c holds (re, im) of spin s, colour c
+    // (each word decoded whole, as the scalar path does: fp16 pairs convert
+    // in one instruction)
+    constexpr int qa = (MU == 2) ? 2 : 3, qb = (MU == 2) ? 3 : 2;
+    constexpr float s = (float)((MU == 1) ? -S : S);
+    float2 pw[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) pw[j] = In::pair(sw[j]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 pr = make_float2(pw[c].x, pw[3 + c].x);
+      const float2 pi = make_float2(pw[c].y, pw[3 + c].y);
+      const float2 qr = make_float2(pw[qa * 3 + c].x, pw[qb * 3 + c].x);
+      const float2 qi = make_float2(pw[qa * 3 + c].y, pw[qb * 3 + c].y);
+      if constexpr (MU == 0) {  // h0 = p0 + s i p3, h1 = p1 + s i p2
+        hr[c] = __ffma2_rn(dup2(-s), qi, pr);
+        hi[c] = __ffma2_rn(dup2(s), qr, pi);
+      } else if constexpr (MU == 1) {  // h0 = p0 - s p3, h1 = p1 + s p2
+        hr[c] = __ffma2_rn(make_float2(-s, s), qr, pr);
+        hi[c] = __ffma2_rn(make_float2(-s, s), qi, pi);
+      } else {  // h0 = p0 + s i p2, h1 = p1 - s i p3
+        hr[c] = __ffma2_rn(make_float2(-s, s), qi, pr);
+        hi[c] = __ffma2_rn(make_float2(s, -s), qr, pi);
+      }
+    }
+    float2 gr[3], gi[3];
+    su3_mul_pairs<!FWD>(u, hr, hi, gr, gi);
+    reconstruct_pairs<MU, S>(gr, gi, acc, w);
+  } else {
+    constexpr bool upper = (S == +1);
+    uint32_t hw[6];
+    if constexpr (upper) {
+      const uint4 a = sm.sp[H::ST][0][tid];
+      const uint2 b = *reinterpret_cast<const uint2*>(&sm.sp[H::ST][1][tid]);
+      hw[0] = a.x; hw[1] = a.y; hw[2] = a.z; hw[3] = a.w; hw[4] = b.x; hw[5] = b.y;
+    } else {
+      const uint2 a = *reinterpret_cast<const uint2*>(&sm.sp[H::ST][0][tid]);
+      const uint4 b = sm.sp[H::ST][1][tid];
+      hw[0] = a.x; hw[1] = a.y; hw[2] = b.x; hw[3] = b.y; hw[4] = b.z; hw[5] = b.w;
+    }
+    // rows of the half spinor: (spin 0, spin 1) upper; (spin 3, spin 2) lower,
+    // the order of the accumulator pairs
+    constexpr int ra = upper ? 0 : 3, rb = upper ? 3 : 0;
+    float2 pw[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) pw[j] = In::pair(hw[j]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      hr[c] = make_float2(pw[ra + c].x, pw[rb + c].x);
+      hi[c] = make_float2(pw[ra + c].y, pw[rb + c].y);
+    }
+    const bool flip = g.tbc_anti && (FWD ? top : bot);
+    const float2 t2 = dup2(flip ? -2.f * w : 2.f * w);
+    constexpr int o = upper ? 0 : 6;
+    if (unit) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[o + 2 * c] = __ffma2_rn(t2, hr[c], acc[o + 2 * c]);
+        acc[o + 2 * c + 1] = __ffma2_rn(t2, hi[c], acc[o + 2 * c + 1]);
+      }
+    } else {
+      float2 gr[3], gi[3];
+      su3_mul_pairs<!FWD>(u, hr, hi, gr, gi);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[o + 2 * c] = __ffma2_rn(t2, gr[c], acc[o + 2 * c]);
+        acc[o + 2 * c + 1] = __ffma2_rn(t2, gi[c], acc[o + 2 * c + 1]);
+      }
+    }
+  }
+}
+
+template <int K, bool DAGGER, bool TFIX, class In, class G>
+__device__ __forceinline__ void async_step_pairs(AsyncSlots& sm, const Geom& g, const In& in, const G& gauge,
+                                                 int parity, int h, const int (&nb)[8], bool top, bool bot,
+                                                 float2 (&acc)[12]) {
+  if constexpr (K + 2 < 8) async_issue<K + 2, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
+  cp_commit();
+  cp_wait<2>();  // the copies of hop K have landed
+  async_hop_pairs<K, DAGGER, TFIX, In, G>(sm, g, top, bot, acc);
+}
+
 template <int K, bool DAGGER, bool TFIX, class In, class G>
 __device__ __forceinline__ void async_step(AsyncSlots& sm, const Geom& g, const In& in, const G& gauge, int parity,
                                            int h, const int (&nb)[8], bool top, bool bot, float (&acc)[24]) {
@@ -187,12 +370,36 @@ __device__ __forceinline__ void dslash_site_async(const Geom& g, const In& in, c
     nb[7] = (t == 0) ? h + g.wt : h - g.XhYZ;
   }
   const bool top = (t == g.T - 1), bot = (t == 0);
-#pragma unroll
-  for (int k = 0; k < 24; ++k) acc[k] = 0.f;
   async_issue<0, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
   cp_commit();
   async_issue<1, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
   cp_commit();
+  if constexpr (kSpinPairs) {
+    float2 a2[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a2[k] = make_float2(0.f, 0.f);
+    async_step_pairs<0, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<1, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<2, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<3, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<4, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<5, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<6, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+    async_step_pairs<7, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, a2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int ri = 0; ri < 2; ++ri) {
+        acc[(0 + c) * 2 + ri] = a2[2 * c + ri].x;
+        acc[(3 + c) * 2 + ri] = a2[2 * c + ri].y;
+        acc[(9 + c) * 2 + ri] = a2[6 + 2 * c + ri].x;
+        acc[(6 + c) * 2 + ri] = a2[6 + 2 * c + ri].y;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 24; ++k) acc[k] = 0.f;
   async_step<0, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
   async_step<1, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);
   async_step<2, DAGGER, TFIX>(sm, g, in, gauge, parity, h, nb, top, bot, acc);

@@ -310,13 +310,8 @@ struct Spinor16 {
   __device__ __forceinline__ void load(int h, R (&v)[24]) const {
     float f[24];
     const float s = load_raw(h, f);
-    const float2 ss = make_float2(s, s);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const float2 q = __fmul2_rn(make_float2(f[2 * k], f[2 * k + 1]), ss);
-      v[2 * k] = (R)q.x;
-      v[2 * k + 1] = (R)q.y;
-    }
+    for (int k = 0; k < 24; ++k) v[k] = (R)__fmul_rn(f[k], s);
   }
 
   static __device__ __forceinline__ float f32(double d) { return __double2float_rn(d); }
@@ -342,34 +337,27 @@ struct Spinor16 {
       // |fl(f * scale)| <= 32767 (1 + 2^-24)^2 < 2^22 (so no clamp is needed
       // either: m is the largest |f|); the low 16 bits of s are then q in two's
       // complement, and s - 1.5 * 2^23 = q exactly
-      // (both values of a word by one packed multiply and one packed add)
       constexpr float kMagic = 12582912.0f;
-      const float2 sc = make_float2(scale, scale), mg = make_float2(kMagic, kMagic);
-      float2 sv[12];
+      float sv[24];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) sv[k] = __fadd2_rn(__fmul2_rn(make_float2(f[2 * k], f[2 * k + 1]), sc), mg);
+      for (int k = 0; k < 24; ++k) sv[k] = __fadd_rn(__fmul_rn(f[k], scale), kMagic);
       uint32_t w[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) w[k] = __byte_perm(__float_as_uint(sv[k].x), __float_as_uint(sv[k].y), 0x5410);
+      for (int k = 0; k < 12; ++k) w[k] = __byte_perm(__float_as_uint(sv[2 * k]), __float_as_uint(sv[2 * k + 1]), 0x5410);
 #pragma unroll
       for (int c = 0; c < 3; ++c) p[(size_t)c * stride + h] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
       norm[h] = m;
       const float d = __fmul_rn(m, kInv32767);
-      const float2 dd = make_float2(d, d), nmg = make_float2(-kMagic, -kMagic);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const float2 q = __fmul2_rn(__fadd2_rn(sv[k], nmg), dd);
-        v[2 * k] = (R)q.x;
-        v[2 * k + 1] = (R)q.y;
-      }
+      for (int k = 0; k < 24; ++k) v[k] = (R)__fmul_rn(__fsub_rn(sv[k], kMagic), d);
       return;
     }
-    // fp16 / bf16: both values of a word scaled by one packed multiply and
-    // rounded (to nearest, ties to even, each) by one packing conversion
+    // fp16 / bf16: both values of a word rounded (to nearest, ties to even,
+    // each) by one packing conversion
     uint32_t w[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const float2 t = __fmul2_rn(make_float2(f[2 * k], f[2 * k + 1]), make_float2(scale, scale));
+      const float2 t = make_float2(__fmul_rn(f[2 * k], scale), __fmul_rn(f[2 * k + 1], scale));
       if constexpr (F == Fmt16::H16) {
         const __half2 q = __floats2half2_rn(t.x, t.y);
         w[k] = *reinterpret_cast<const uint32_t*>(&q);
@@ -381,12 +369,11 @@ struct Spinor16 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[(size_t)c * stride + h] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
     norm[h] = m;
-    const float2 dd = make_float2(m, m);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const float2 q = __fmul2_rn(pair(w[k]), dd);
-      v[2 * k] = (R)q.x;
-      v[2 * k + 1] = (R)q.y;
+      const float2 q = pair(w[k]);
+      v[2 * k] = (R)__fmul_rn(q.x, m);
+      v[2 * k + 1] = (R)__fmul_rn(q.y, m);
     }
   }
   template <typename R>

@@ -65,7 +65,8 @@ struct PrecOps {
   // S6 BiCGstab iteration and S9 reliable update with this inner precision
   void (*bicg_iteration)(const Ctx&, struct SolveBufs&, cudaStream_t);
   void (*bicg_update)(const Ctx&, struct SolveBufs&, cudaStream_t);
-  void (*bicg_setup)(const Ctx&, struct SolveBufs&, cudaStream_t);
+  // setup from the FP64 even residual src (b_hat, or b_hat - M_hat x0)
+  void (*bicg_setup)(const Ctx&, struct SolveBufs&, const void* src, cudaStream_t);
   // S7 CG on the normal equations, and its reliable update
   void (*cg_iteration)(const Ctx&, struct SolveBufs&, cudaStream_t);
   void (*cg_update)(const Ctx&, struct SolveBufs&, cudaStream_t);
@@ -180,3 +181,8 @@ wd_status wd_internal_ensure_gauge(wd_ctx* ctx, int prec);
 wd_status wd_internal_export_full(wd_ctx* ctx, double* host, const void* even, const void* odd);
 wd_status wd_internal_import_full(wd_ctx* ctx, void* even, void* odd, const double* host);
 wd_status wd_internal_export_full_async(wd_ctx* ctx, double* host, const void* even, const void* odd);
+// wd_solve_device (BiCGstab) started from the even half of x_full instead of
+// zero: the iteration begins with the FP64 residual b_hat - M_hat x0_e (a
+// reliable update at iteration 0); the odd half of x_full is overwritten
+wd_status wd_internal_solve_x0(wd_ctx* ctx, void* x_full, const void* b_full, double kappa,
+                               const wd_solve_params* params, wd_solve_info* info);

@@ -572,12 +572,11 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // few more registers, and the FP64 kernel is bound by the FP64 pipe.
 template <typename R, class In, int NRED, bool TFIX, bool R8>
 struct DslashOccupancy {
-  // (the Q16 temporal-gauge store kernel spills at 5 blocks and runs 3 %
-  // faster at 4; the fp16 / bf16 ones are 1-2 % faster at 5)
+  // (the 16-bit temporal-gauge kernels spill at 5 blocks with the
+  // spin-paired arithmetic)
   static constexpr int kMinBlocks = (sizeof(R) == 8)       ? 3
                                     : R8                  ? (NRED == 0 ? 4 : 3)
-                                    : In::kScaled         ? (TFIX ? (NRED == 0 ? (In::kIntCodes ? 4 : 5) : 4)
-                                                                  : (NRED == 0 ? 6 : 5))
+                                    : In::kScaled         ? (TFIX ? 4 : (NRED == 0 ? 6 : 5))
                                                           : (NRED == 0 ? 5 : 4);
 };
 
@@ -1206,9 +1205,9 @@ struct Impl {
     else launch_sites(c, c.g.Vh, OpAccumulate<S>{T64::view(b.x, c.g), T::view(b.x_hat, c.g)}, s);
   }
 
-  static void bicg_setup(const Ctx& c, SolveBufs& b, cudaStream_t s) {
+  static void bicg_setup(const Ctx& c, SolveBufs& b, const void* src, cudaStream_t s) {
     using Q = OpQuantDup<S, SpinorF64, FinBicgSetup>;
-    launch_sites(c, c.g.Vh, Q{T::view(b.r_hat, c.g), T::view(b.r_tilde, c.g), T64::view(b.b_hat, c.g), c.red,
+    launch_sites(c, c.g.Vh, Q{T::view(b.r_hat, c.g), T::view(b.r_tilde, c.g), T64::view(src, c.g), c.red,
                                FinBicgSetup{b.ctl}}, s);
     zero(c, b.p, s);
     zero(c, b.v, s);

@@ -338,7 +338,7 @@ wd_status admit(wd_server* sv, Pool& pl, Request& q, int r) {
   o64->zero(c, s.x, c.stream);
   slot_init_kernel<<<1, 1, 0, c.stream>>>(s.ctl, q.tol, prec == WD_F64 ? 0.0 : sv->p.delta, sv->p.max_iter, q.kappa,
                                           sc);
-  prec_ops(prec)->bicg_setup(c, s, c.stream);
+  prec_ops(prec)->bicg_setup(c, s, s.b_hat, c.stream);
   WS_CK(sv, cudaGetLastError());
   pl.slot_req[r] = q.id;
   q.state = 1;
