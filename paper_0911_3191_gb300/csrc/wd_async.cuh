@@ -374,7 +374,7 @@ __device__ __forceinline__ void dslash_site_async(const Geom& g, const In& in, c
   cp_commit();
   async_issue<1, DAGGER, TFIX>(sm, in, gauge, parity, h, nb, top, bot);
   cp_commit();
-  if constexpr (kSpinPairs) {
+  if constexpr (kSpinPairs && In::kPairedHops) {
     float2 a2[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) a2[k] = make_float2(0.f, 0.f);

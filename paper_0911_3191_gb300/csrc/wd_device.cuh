@@ -99,6 +99,7 @@ struct SpinorF64 {
   using real = double;
   static constexpr bool kScaled = false;
   static constexpr bool kIntCodes = false;
+  static constexpr bool kPairedHops = false;
   double2* p;
   int stride;
   size_t rs;  // bytes from one right-hand side's field to the next (batches)
@@ -144,6 +145,7 @@ struct SpinorF32 {
   using real = float;
   static constexpr bool kScaled = false;
   static constexpr bool kIntCodes = false;
+  static constexpr bool kPairedHops = false;
   float4* p;
   int stride;
   size_t rs;
@@ -249,6 +251,10 @@ struct Spinor16 {
   }
   // integer codes (Q16): the launch shapes of their kernels differ
   static constexpr bool kIntCodes = (F == Fmt16::Q16);
+  // spin-paired hops (wd_async.cuh) for Q16 and bf16, whose decodes run on the
+  // conversion and integer pipes; fp16 decodes run on the FMA pipe, which the
+  // paired arithmetic keeps full, and fp16 is faster with the scalar hops
+  static constexpr bool kPairedHops = (F != Fmt16::H16);
   // the factor that turns raw values into field values, from the site norm
   static __device__ __forceinline__ float scale_of(float n) {
     if constexpr (F == Fmt16::Q16) return __fmul_rn(n, kInv32767);

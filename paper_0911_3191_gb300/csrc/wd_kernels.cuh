@@ -572,12 +572,13 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // few more registers, and the FP64 kernel is bound by the FP64 pipe.
 template <typename R, class In, int NRED, bool TFIX, bool R8>
 struct DslashOccupancy {
-  // (the 16-bit temporal-gauge kernels spill at 5 blocks with the
-  // spin-paired arithmetic)
-  static constexpr int kMinBlocks = (sizeof(R) == 8)       ? 3
-                                    : R8                  ? (NRED == 0 ? 4 : 3)
-                                    : In::kScaled         ? (TFIX ? 4 : (NRED == 0 ? 6 : 5))
-                                                          : (NRED == 0 ? 5 : 4);
+  // (the 16-bit temporal-gauge kernels with spin-paired hops spill at 5
+  // blocks; the fp16 one, with scalar hops, is 1-2 % faster at 5)
+  static constexpr int kMinBlocks = (sizeof(R) == 8) ? 3
+                                    : R8            ? (NRED == 0 ? 4 : 3)
+                                    : In::kScaled   ? (TFIX ? ((NRED == 0 && !In::kPairedHops) ? 5 : 4)
+                                                            : (NRED == 0 ? 6 : 5))
+                                                    : (NRED == 0 ? 5 : 4);
 };
 
 // 16-bit spinors with 12-real links take the cp.async pipeline of
