@@ -245,13 +245,30 @@ void wo_apply_Mhat(double *out, const double *in, const double *U, const int dim
 
 /* ---------------------------------------------------------------- solvers */
 
+/* Sec. 5.1: global sums in FP64.  The index range is cut into a fixed number
+ * of chunks, each summed in index order, and the chunk sums are added in chunk
+ * order: the result does not depend on the number of threads or on their
+ * timing (an OpenMP reduction clause combines the threads' partial sums in an
+ * unspecified order, so its last bits varied from run to run). */
+enum { kDotChunks = 256 };
 static cd dot(const cd *a, const cd *b, int64_t n) {
+  double pre[kDotChunks], pim[kDotChunks];
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < kDotChunks; ++c) {
+    const int64_t i0 = n * c / kDotChunks, i1 = n * (c + 1) / kDotChunks;
+    double re = 0.0, im = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+      cd p = conj(a[i]) * b[i];
+      re += creal(p);
+      im += cimag(p);
+    }
+    pre[c] = re;
+    pim[c] = im;
+  }
   double re = 0.0, im = 0.0;
-#pragma omp parallel for reduction(+ : re, im) schedule(static)
-  for (int64_t i = 0; i < n; ++i) {
-    cd p = conj(a[i]) * b[i];
-    re += creal(p);
-    im += cimag(p);
+  for (int c = 0; c < kDotChunks; ++c) {
+    re += pre[c];
+    im += pim[c];
   }
   return re + I * im;
 }
