@@ -225,6 +225,13 @@ typedef struct {
                           updates, is kept in FP32 when the inner precision is
                           16-bit (Sec. 5.3 keeps it in the inner precision, the
                           default 0); single solves only                        */
+  int initial_guess;   /* 1: start from the x passed in (its even half; the odd
+                          half is rebuilt from it): the accumulator holds x_e
+                          and the first step is the FP64 residual b_hat -
+                          M_hat x_e, a reliable update at iteration 0; an x
+                          that already meets tol returns after no iteration.
+                          BiCGstab with reliable updates (restart 0) only;
+                          single solves only.  0 (default): start from zero */
 } wd_solve_params;
 
 typedef struct {

@@ -42,7 +42,7 @@ class WDError(RuntimeError):
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("solver", ctypes.c_int), ("inner_precision", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("restart", ctypes.c_int), ("xhat_f32", ctypes.c_int)]
+                ("restart", ctypes.c_int), ("xhat_f32", ctypes.c_int), ("initial_guess", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -281,13 +281,15 @@ class WilsonDirac:
         return r.value
 
     @staticmethod
-    def _params(tol, delta, max_iter, solver, inner_precision, use_graph, restart=False, xhat_f32=False):
+    def _params(tol, delta, max_iter, solver, inner_precision, use_graph, restart=False, xhat_f32=False,
+                initial_guess=False):
         return SolveParams(float(tol), float(delta), int(max_iter), int(solver), int(inner_precision),
-                           int(use_graph), int(bool(restart)), int(bool(xhat_f32)))
+                           int(use_graph), int(bool(restart)), int(bool(xhat_f32)), int(bool(initial_guess)))
 
     def _solve(self, fn, x, b, kappa, tol, delta, max_iter, solver, inner_precision, use_graph, check,
-               restart=False, xhat_f32=False):
-        p = self._params(tol, delta, max_iter, solver, inner_precision, use_graph, restart, xhat_f32)
+               restart=False, xhat_f32=False, initial_guess=False):
+        p = self._params(tol, delta, max_iter, solver, inner_precision, use_graph, restart, xhat_f32,
+                         initial_guess)
         info = SolveInfo()
         st = fn(self.ctx, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), ctypes.byref(info))
         if check and st not in (0,):
@@ -299,19 +301,20 @@ class WilsonDirac:
                            int(info.kernel_launches))
 
     def solve(self, x, b, kappa, tol=1e-12, delta=0.1, max_iter=20000, solver=BICGSTAB, inner_precision=F64,
-              use_graph=True, check=True, restart=False, xhat_f32=False) -> SolveResult:
+              use_graph=True, check=True, restart=False, xhat_f32=False, initial_guess=False) -> SolveResult:
         """x, b: (V, 4, 3) complex128 host arrays (pinned torch tensors also work).
         restart=True: defect correction (Alg. 1) with eps_in = delta.
-        xhat_f32=True: x_hat in FP32 under a 16-bit inner precision."""
+        xhat_f32=True: x_hat in FP32 under a 16-bit inner precision.
+        initial_guess=True: start from the x passed in (BiCGstab, reliable updates)."""
         return self._solve(self.lib.wd_solve, x, b, kappa, tol, delta, max_iter, solver, inner_precision,
-                           use_graph, check, restart, xhat_f32)
+                           use_graph, check, restart, xhat_f32, initial_guess)
 
     def solve_device(self, x, b, kappa, tol=1e-12, delta=0.1, max_iter=20000, solver=BICGSTAB,
                      inner_precision=F64, use_graph=True, check=True, restart=False,
-                     xhat_f32=False) -> SolveResult:
+                     xhat_f32=False, initial_guess=False) -> SolveResult:
         """x, b: device FP64 full fields (``new_field(F64, 2)``)."""
         return self._solve(self.lib.wd_solve_device, x, b, kappa, tol, delta, max_iter, solver, inner_precision,
-                           use_graph, check, restart, xhat_f32)
+                           use_graph, check, restart, xhat_f32, initial_guess)
 
     def dslash_batch(self, out, inp, nrhs: int, out_parity: int, dagger: bool, prec: int):
         """out_r = D in_r for nrhs single-parity fields stored back to back."""

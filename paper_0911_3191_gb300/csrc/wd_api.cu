@@ -570,6 +570,9 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   if (p.restart && p.inner_precision == WD_F64)
     return set_err(ctx, WD_ERR_INVALID_ARG, "defect correction needs a lower inner precision");
   if (p.solver != WD_BICGSTAB && p.solver != WD_CGNR) return set_err(ctx, WD_ERR_INVALID_ARG, "bad solver");
+  if (p.initial_guess != 0 && p.initial_guess != 1)
+    return set_err(ctx, WD_ERR_INVALID_ARG, "initial_guess must be 0 or 1");
+  x0 = x0 || p.initial_guess;
   if (x0 && (p.solver != WD_BICGSTAB || p.restart))
     return set_err(ctx, WD_ERR_INVALID_ARG, "an initial guess needs BiCGstab with reliable updates");
   if (!(p.tol > 0.0) || p.max_iter <= 0) return set_err(ctx, WD_ERR_INVALID_ARG, "bad tol or max_iter");
@@ -1137,9 +1140,14 @@ wd_status wd_solve(wd_ctx* ctx, double* x, const double* b, double kappa, const 
   if ((st = ensure_staging(ctx)) != WD_OK) return st;
   const size_t lex_bytes = (size_t)2 * c.g.Vh * 24 * sizeof(double);
   const PrecOps* o64 = ops_f64();
-  WD_CK(ctx, cudaMemcpyAsync(c.lex_staging, b, lex_bytes, cudaMemcpyHostToDevice, c.stream));
   char* bf = (char*)c.sb_full[0];
   char* xf = (char*)c.sb_full[1];
+  if (params && params->initial_guess == 1) {  // the starting x, through the same staging buffer
+    WD_CK(ctx, cudaMemcpyAsync(c.lex_staging, x, lex_bytes, cudaMemcpyHostToDevice, c.stream));
+    o64->import_lex(c, xf, c.lex_staging, 0, c.stream);
+    o64->import_lex(c, xf + f64, c.lex_staging, 1, c.stream);
+  }
+  WD_CK(ctx, cudaMemcpyAsync(c.lex_staging, b, lex_bytes, cudaMemcpyHostToDevice, c.stream));
   o64->import_lex(c, bf, c.lex_staging, 0, c.stream);
   o64->import_lex(c, bf + f64, c.lex_staging, 1, c.stream);
   WD_CK_LAUNCH(ctx, "wd_solve import");

@@ -573,6 +573,7 @@ wd_status multishift_core(wd_ctx* ctx, int n, char* x, const char* b, const doub
     wd_solve_params p2 = *params;
     p2.solver = WD_BICGSTAB;
     p2.restart = 0;
+    p2.initial_guess = 0;  // the start is x_e itself (wd_internal_solve_x0)
     wd_solve_info ie{};
     const wd_status se = wd_internal_solve_x0(ctx, xfull, b, kap, &p2, &ie);
     if (se != WD_OK && se != WD_ERR_NOT_CONVERGED) return se;

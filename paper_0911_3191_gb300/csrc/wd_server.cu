@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -79,6 +81,15 @@ struct Pin {
   bool registered = false;
 };
 
+// One completed step of a pool, for the optional trace (WD_SERVER_TRACE)
+struct StepRecord {
+  double t_end;    // seconds since the server was created, when the step was seen complete
+  int pool;
+  int capacity;    // slots of the pool's workspace
+  int active;      // slots holding a request during the step
+  double step_ms;  // device time of the step (events around its iterations)
+};
+
 struct wd_server {
   wd_server_params p;
   std::vector<Pool> pools;
@@ -92,6 +103,11 @@ struct wd_server {
   long long next_id = 1;
   std::string err;
   wd_server_stats st{};
+  // optional trace of every completed step, written as CSV to the file named
+  // by WD_SERVER_TRACE when the server is destroyed (empty: no trace)
+  std::string trace_path;
+  std::vector<StepRecord> trace;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
 
 namespace {
@@ -445,6 +461,11 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& d
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, pl.start_ev, pl.done_ev) == cudaSuccess) s->st.gpu_step_seconds += 1e-3 * ms;
     else cudaGetLastError();
+    if (!s->trace_path.empty()) {
+      int active = 0;
+      for (long long id : pl.slot_req) active += (id >= 0);
+      s->trace.push_back(StepRecord{since(s->t0), (int)(&pl - s->pools.data()), pl.capacity, active, (double)ms});
+    }
     // retire the slots whose system finished during the step just completed
     WS_CK(s, cudaMemcpyAsync(pl.hctl, pl.bb.ctl, pl.capacity * sizeof(SolverCtl), cudaMemcpyDeviceToHost, c.stream));
     WS_CK(s, cudaStreamSynchronize(c.stream));
@@ -534,12 +555,24 @@ wd_status wd_server_create(wd_server** out, const wd_server_params* p) {
   wd_server* s = new (std::nothrow) wd_server();
   if (!s) return WD_ERR_OOM;
   s->p = *p;
+  if (const char* tp = std::getenv("WD_SERVER_TRACE")) s->trace_path = tp;
   *out = s;
   return WD_OK;
 }
 
 wd_status wd_server_destroy(wd_server* s) {
   if (!s) return WD_OK;
+  if (!s->trace_path.empty()) {
+    if (FILE* f = std::fopen(s->trace_path.c_str(), "w")) {
+      std::fprintf(f, "t_end_s,pool,dims,capacity,active,step_ms\n");
+      for (const StepRecord& r : s->trace) {
+        const Pool& pl = s->pools[r.pool];
+        std::fprintf(f, "%.6f,%d,%dx%dx%dx%d,%d,%d,%.4f\n", r.t_end, r.pool, pl.dims[0], pl.dims[1], pl.dims[2],
+                     pl.dims[3], r.capacity, r.active, r.step_ms);
+      }
+      std::fclose(f);
+    }
+  }
   for (Pool& pl : s->pools)
     if (pl.ctx) cudaStreamSynchronize(pl.ctx->c.stream);
   for (auto& kv : s->reqs) {

@@ -250,6 +250,7 @@ wd_status solve_batch_device(wd_ctx* ctx, int n, void* x, const void* bsrc, cons
     return berr(ctx, WD_ERR_INVALID_ARG, "bad inner_precision");
   if (p.solver != WD_BICGSTAB) return berr(ctx, WD_ERR_INVALID_ARG, "batched solves use BiCGstab");
   if (p.restart) return berr(ctx, WD_ERR_INVALID_ARG, "batched solves use reliable updates (restart = 0)");
+  if (p.initial_guess) return berr(ctx, WD_ERR_INVALID_ARG, "batched solves start from zero (initial_guess = 0)");
   if (!(p.tol > 0.0) || p.max_iter <= 0) return berr(ctx, WD_ERR_INVALID_ARG, "bad tol or max_iter");
   if (p.inner_precision == WD_F64) p.delta = 0.0;
   else if (!(p.delta > 0.0 && p.delta < 1.0)) return berr(ctx, WD_ERR_INVALID_ARG, "delta must be in (0,1)");

@@ -211,3 +211,53 @@ def test_status_ok_implies_reported_residual_below_tol(small, solver, prec):
             assert r.true_rel_residual <= tol and rel <= tol * (1 + 1e-6), (tol, r, rel)
         else:
             assert r.status == 4 and r.true_rel_residual > tol, (tol, r)
+
+
+@pytest.mark.parametrize("prec", [0, 2, 4])
+def test_initial_guess_from_a_rough_solution(small, prec):
+    """initial_guess: a solve to 1e-4 followed by one to 1e-12 started from
+    its x reaches the tolerance (checked by the oracle), with fewer
+    iterations than from zero; the first step is the FP64 residual of the
+    start (one reliable update)."""
+    m, wd, dims, kappa, U, b, x_ref, _ = small
+    x = np.zeros_like(b)
+    r0 = wd.solve(x, b, kappa, tol=1e-12, solver=0, inner_precision=prec)
+    x = np.zeros_like(b)
+    rough = wd.solve(x, b, kappa, tol=1e-4, solver=0, inner_precision=prec)
+    assert rough.status == 0 and oracle.true_residual(x, b, U, dims, kappa) <= 1e-4
+    r = wd.solve(x, b, kappa, tol=1e-12, solver=0, inner_precision=prec, initial_guess=True)
+    rel = oracle.true_residual(x, b, U, dims, kappa)
+    assert r.status == 0 and rel <= 1e-12, (prec, r, rel)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-9
+    assert r.reliable_updates >= 1
+    assert r.iters < r0.iters, (r.iters, r0.iters)
+
+
+def test_initial_guess_that_meets_tol_returns_at_once(small):
+    """Started from a solution that already meets tol (on the device, from
+    device fields), the solve runs no iteration; the returned x keeps its
+    even half and gets the odd half rebuilt from it, with the same residual
+    to rounding."""
+    import torch
+    m, wd, dims, kappa, U, b, _, _ = small
+    fb = wd.upload(b, m.F64)
+    fx = wd.new_field(m.F64, 2)
+    r1 = wd.solve_device(fx, fb, kappa, tol=1e-10, solver=0, inner_precision=2)
+    assert r1.status == 0
+    before = fx.clone()
+    r2 = wd.solve_device(fx, fb, kappa, tol=1e-10, solver=0, inner_precision=2, initial_guess=True)
+    torch.cuda.synchronize()
+    assert r2.status == 0 and r2.iters == 0 and r2.reliable_updates == 0, r2
+    half = fx.numel() // 2
+    assert torch.equal(fx[:half], before[:half])
+    rel2 = r2.true_rel_residual
+    assert rel2 <= 1e-10 and abs(rel2 - r1.true_rel_residual) <= 1e-3 * r1.true_rel_residual + 1e-15
+
+
+def test_initial_guess_needs_bicgstab_with_reliable_updates(small):
+    m, wd, dims, kappa, U, b, _, _ = small
+    x = np.zeros_like(b)
+    with pytest.raises(m.WDError):
+        wd.solve(x, b, kappa, tol=1e-8, solver=1, inner_precision=2, initial_guess=True)
+    with pytest.raises(m.WDError):
+        wd.solve(x, b, kappa, tol=1e-8, solver=0, inner_precision=2, restart=True, initial_guess=True)
