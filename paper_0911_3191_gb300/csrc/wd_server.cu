@@ -65,8 +65,20 @@ struct Pool {
   std::deque<long long> queue;
   SolverCtl* hctl = nullptr;        // pinned mirror of the ctl array
   bool launched = false;            // a step of iterations is in flight
+  int trace_idx = -1;               // its record in the server's trace (WD_SERVER_TRACE)
   cudaEvent_t start_ev = nullptr;   // recorded before the step's iterations
   cudaEvent_t done_ev = nullptr;    // recorded after them
+  // the source of the next queued request, uploaded on a stream of its own
+  // while the pool's steps run (host layout, one full field)
+  void* pf_buf = nullptr;
+  cudaStream_t pf_stream = nullptr;
+  cudaEvent_t pf_done = nullptr;    // the upload into pf_buf has completed
+  cudaEvent_t pf_free = nullptr;    // the admission has read pf_buf
+  long long pf_req = -1;            // request whose source is in pf_buf (or on its way)
+  cudaEvent_t turn_ev = nullptr;    // trace: recorded before the retire and admit work
+  cudaEvent_t seg_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // trace: ends of the turnover segments
+  bool seg_used = false;            // trace: a retire and an admission ran in this turnover
+  double t_seen = 0.0;              // trace: when the last step was seen complete
 };
 
 }  // namespace
@@ -83,11 +95,16 @@ struct Pin {
 
 // One completed step of a pool, for the optional trace (WD_SERVER_TRACE)
 struct StepRecord {
-  double t_end;    // seconds since the server was created, when the step was seen complete
+  double t_launch;  // seconds since the server was created, when the step was launched
+  double t_end;     // ... when the step was seen complete
   int pool;
-  int capacity;    // slots of the pool's workspace
-  int active;      // slots holding a request during the step
-  double step_ms;  // device time of the step (events around its iterations)
+  int capacity;     // slots of the pool's workspace
+  int active;       // slots holding a request during the step
+  int admitted;     // requests admitted just before the step
+  double step_ms;   // device time of the step (events around its iterations)
+  double turn_ms;   // device time from the previous step's end to this one's start (retire, admit)
+  double host_ms;   // host time from seeing the previous step complete to this launch
+  double seg_ms[4]; // of turn_ms: retire kernels, export + download, upload + import, admission kernels
 };
 
 struct wd_server {
@@ -107,6 +124,7 @@ struct wd_server {
   // by WD_SERVER_TRACE when the server is destroyed (empty: no trace)
   std::string trace_path;
   std::vector<StepRecord> trace;
+  long long pins_registered = 0, pins_pageable = 0;  // host buffers page-locked / left pageable
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
 
@@ -126,6 +144,7 @@ void pin(wd_server* s, const void* p, size_t bytes) {
   cudaGetLastError();
   pn.registered = cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterDefault) == cudaSuccess;
   if (!pn.registered) cudaGetLastError();  // pageable: transfers stay correct, just synchronous
+  ++(pn.registered ? s->pins_registered : s->pins_pageable);
 }
 
 void unpin(wd_server* s, const void* p) {
@@ -343,8 +362,22 @@ wd_status admit(wd_server* sv, Pool& pl, Request& q, int r) {
   const int prec = sv->p.inner_precision;
   const size_t f64 = fbytes(c, WD_F64);
   char* bf = (char*)pl.bfull + 2 * f64 * r;
-  wd_status st = wd_internal_import_full(pl.ctx, bf, bf + f64, q.b);
-  if (st != WD_OK) return serr(sv, st, std::string("source upload: ") + wd_last_error(pl.ctx));
+  const bool seg = !sv->trace_path.empty() && pl.seg_ev[1];
+  if (seg) WS_CK(sv, cudaEventRecord(pl.seg_ev[2], c.stream));
+  if (pl.pf_req == q.id) {  // uploaded ahead: convert from the prefetch buffer
+    WS_CK(sv, cudaStreamWaitEvent(c.stream, pl.pf_done, 0));
+    ops_f64()->import_lex(c, bf, (const double*)pl.pf_buf, 0, c.stream);
+    ops_f64()->import_lex(c, bf + f64, (const double*)pl.pf_buf, 1, c.stream);
+    WS_CK(sv, cudaEventRecord(pl.pf_free, c.stream));
+    pl.pf_req = -1;
+  } else {
+    wd_status st = wd_internal_import_full(pl.ctx, bf, bf + f64, q.b);
+    if (st != WD_OK) return serr(sv, st, std::string("source upload: ") + wd_last_error(pl.ctx));
+  }
+  if (seg) {
+    WS_CK(sv, cudaEventRecord(pl.seg_ev[3], c.stream));
+    pl.seg_used = true;
+  }
   const PrecOps* o64 = ops_f64();
   SolveBufs s = slot_bufs(pl, r, prec);
   double* sc = pl.bb.scal + 4 * r;
@@ -407,8 +440,14 @@ wd_status retire(wd_server* sv, Pool& pl, Request& q, int r, const SolverCtl& hc
   sv->scal_free.pop_back();
   WS_CK(sv, cudaMemcpyAsync(sv->scal_pinned + 4 * q.scal_idx, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             c.stream));
+  if (!sv->trace_path.empty()) {
+    for (cudaEvent_t& e : pl.seg_ev)
+      if (!e) WS_CK(sv, cudaEventCreate(&e));
+    WS_CK(sv, cudaEventRecord(pl.seg_ev[0], c.stream));
+  }
   const wd_status st = wd_internal_export_full_async(pl.ctx, q.x, s.x, s.tmp64);
   if (st != WD_OK) return serr(sv, st, std::string("solution download: ") + wd_last_error(pl.ctx));
+  if (!sv->trace_path.empty()) WS_CK(sv, cudaEventRecord(pl.seg_ev[1], c.stream));
   q.final_ctl = hc;
   if (!q.done_ev) WS_CK(sv, cudaEventCreateWithFlags(&q.done_ev, cudaEventDisableTiming));
   WS_CK(sv, cudaEventRecord(q.done_ev, c.stream));
@@ -449,6 +488,21 @@ wd_status finish(wd_server* sv, Request& q) {
   return WD_OK;
 }
 
+// Upload the source of the pool's next queued request into its prefetch
+// buffer, on the prefetch stream, so that the copy overlaps the pool's steps
+// (the admission then only converts it); after the previous admission has
+// read the buffer.
+wd_status prefetch(wd_server* s, Pool& pl) {
+  if (!pl.pf_buf || pl.pf_req >= 0 || pl.queue.empty()) return WD_OK;
+  const Request& q = s->reqs[pl.queue.front()];
+  const size_t bytes = (size_t)2 * pl.ctx->c.g.Vh * 24 * sizeof(double);
+  WS_CK(s, cudaStreamWaitEvent(pl.pf_stream, pl.pf_free, 0));
+  WS_CK(s, cudaMemcpyAsync(pl.pf_buf, q.b, bytes, cudaMemcpyHostToDevice, pl.pf_stream));
+  WS_CK(s, cudaEventRecord(pl.pf_done, pl.pf_stream));
+  pl.pf_req = q.id;
+  return WD_OK;
+}
+
 // One pool: retire finished slots, release idle memory, admit, launch.
 // did_work: a step completed, memory moved, a request was admitted or a step
 // launched (a pool that only waits for memory does nothing)
@@ -461,10 +515,25 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& d
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, pl.start_ev, pl.done_ev) == cudaSuccess) s->st.gpu_step_seconds += 1e-3 * ms;
     else cudaGetLastError();
-    if (!s->trace_path.empty()) {
-      int active = 0;
-      for (long long id : pl.slot_req) active += (id >= 0);
-      s->trace.push_back(StepRecord{since(s->t0), (int)(&pl - s->pools.data()), pl.capacity, active, (double)ms});
+    if (!s->trace_path.empty() && pl.trace_idx >= 0) {
+      StepRecord& rec = s->trace[pl.trace_idx];
+      rec.t_end = pl.t_seen = since(s->t0);
+      rec.step_ms = ms;
+      float tm = 0.f;
+      if (pl.turn_ev && cudaEventElapsedTime(&tm, pl.turn_ev, pl.start_ev) == cudaSuccess) rec.turn_ms = tm;
+      else cudaGetLastError();
+      if (pl.seg_used) {
+        const cudaEvent_t a[4] = {pl.turn_ev, pl.seg_ev[0], pl.seg_ev[2], pl.seg_ev[3]};
+        const cudaEvent_t b[4] = {pl.seg_ev[0], pl.seg_ev[1], pl.seg_ev[3], pl.start_ev};
+        for (int k = 0; k < 4; ++k) {
+          float sm = 0.f;
+          if (cudaEventElapsedTime(&sm, a[k], b[k]) == cudaSuccess) rec.seg_ms[k] = sm;
+          else cudaGetLastError();
+        }
+        pl.seg_used = false;
+      }
+      if (!pl.turn_ev) WS_CK(s, cudaEventCreate(&pl.turn_ev));
+      WS_CK(s, cudaEventRecord(pl.turn_ev, c.stream));
     }
     // retire the slots whose system finished during the step just completed
     WS_CK(s, cudaMemcpyAsync(pl.hctl, pl.bb.ctl, pl.capacity * sizeof(SolverCtl), cudaMemcpyDeviceToHost, c.stream));
@@ -500,12 +569,14 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& d
       did_work = true;
     }
   }
+  int admitted = 0;
   for (int r = 0; r < pl.capacity && !pl.queue.empty(); ++r) {
     if (pl.slot_req[r] >= 0) continue;
     const long long id = pl.queue.front();
     pl.queue.pop_front();
     wd_status st = admit(s, pl, s->reqs[id], r);
     if (st != WD_OK) return st;
+    ++admitted;
   }
   int n = 0;
   for (long long id : pl.slot_req) n += (id >= 0);
@@ -534,6 +605,13 @@ wd_status pool_progress(wd_server* s, Pool& pl, int& waiting_for_memory, bool& d
   }
   WS_CK(s, cudaEventRecord(pl.done_ev, c.stream));
   pl.launched = true;
+  if (wd_status pst = prefetch(s, pl); pst != WD_OK) return pst;
+  if (!s->trace_path.empty()) {
+    pl.trace_idx = (int)s->trace.size();
+    const double now = since(s->t0);
+    s->trace.push_back(StepRecord{now, 0.0, (int)(&pl - s->pools.data()), pl.capacity, n, admitted, 0.0, 0.0,
+                                  pl.t_seen > 0.0 ? 1e3 * (now - pl.t_seen) : 0.0, {0.0, 0.0, 0.0, 0.0}});
+  }
   did_work = true;
   ++s->st.steps;
   return WD_OK;
@@ -564,17 +642,25 @@ wd_status wd_server_destroy(wd_server* s) {
   if (!s) return WD_OK;
   if (!s->trace_path.empty()) {
     if (FILE* f = std::fopen(s->trace_path.c_str(), "w")) {
-      std::fprintf(f, "t_end_s,pool,dims,capacity,active,step_ms\n");
+      std::fprintf(f, "# host buffers page-locked %lld, left pageable %lld\n", s->pins_registered,
+                   s->pins_pageable);
+      std::fprintf(f,
+                   "t_launch_s,t_end_s,pool,dims,capacity,active,admitted,step_ms,turn_ms,host_ms,"
+                   "retire_ms,download_ms,upload_ms,admit_ms\n");
       for (const StepRecord& r : s->trace) {
         const Pool& pl = s->pools[r.pool];
-        std::fprintf(f, "%.6f,%d,%dx%dx%dx%d,%d,%d,%.4f\n", r.t_end, r.pool, pl.dims[0], pl.dims[1], pl.dims[2],
-                     pl.dims[3], r.capacity, r.active, r.step_ms);
+        std::fprintf(f, "%.6f,%.6f,%d,%dx%dx%dx%d,%d,%d,%d,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f\n", r.t_launch,
+                     r.t_end, r.pool, pl.dims[0], pl.dims[1], pl.dims[2], pl.dims[3], r.capacity, r.active,
+                     r.admitted, r.step_ms, r.turn_ms, r.host_ms, r.seg_ms[0], r.seg_ms[1], r.seg_ms[2],
+                     r.seg_ms[3]);
       }
       std::fclose(f);
     }
   }
-  for (Pool& pl : s->pools)
+  for (Pool& pl : s->pools) {
     if (pl.ctx) cudaStreamSynchronize(pl.ctx->c.stream);
+    if (pl.pf_stream) cudaStreamSynchronize(pl.pf_stream);  // before the host buffers are unregistered
+  }
   for (auto& kv : s->reqs) {
     if (kv.second.state == 3) finish(s, kv.second);
     if (kv.second.done_ev) cudaEventDestroy(kv.second.done_ev);
@@ -588,6 +674,16 @@ wd_status wd_server_destroy(wd_server* s) {
     release_workspace(pl, s->used);
     if (pl.done_ev) cudaEventDestroy(pl.done_ev);
     if (pl.start_ev) cudaEventDestroy(pl.start_ev);
+    if (pl.pf_stream) {
+      cudaStreamSynchronize(pl.pf_stream);
+      cudaStreamDestroy(pl.pf_stream);
+    }
+    if (pl.pf_done) cudaEventDestroy(pl.pf_done);
+    if (pl.pf_free) cudaEventDestroy(pl.pf_free);
+    if (pl.pf_buf) cudaFree(pl.pf_buf);
+    if (pl.turn_ev) cudaEventDestroy(pl.turn_ev);
+    for (cudaEvent_t e : pl.seg_ev)
+      if (e) cudaEventDestroy(e);
     if (pl.ctx) {
       cudaStream_t st = pl.ctx->c.stream;
       wd_destroy(pl.ctx);
@@ -622,6 +718,7 @@ wd_status wd_server_add_gauge(wd_server* s, const int dims[4], int t_antiperiodi
   else if (ip != WD_F64) inner_gauge = links * 24;
   pl.fixed_bytes = links * (recon / 2) * 16 + inner_gauge + (size_t)2 * c.g.Vh * 24 * 8 + ((size_t)c.num_sms * 128 * 8);
   if (s->p.gauge_flags & WD_GAUGE_TEMPORAL) pl.fixed_bytes += (size_t)2 * 9 * c.g.stride * 16;  // G (import / export)
+  pl.fixed_bytes += (size_t)2 * c.g.Vh * 24 * 8;  // prefetch buffer of the next request's source
   if (s->p.budget_bytes && s->used + pl.fixed_bytes > s->p.budget_bytes) {
     wd_destroy(pl.ctx);
     cudaStreamDestroy(st);
@@ -634,6 +731,24 @@ wd_status wd_server_add_gauge(wd_server* s, const int dims[4], int t_antiperiodi
     wd_destroy(pl.ctx);
     cudaStreamDestroy(st);
     return serr(s, r, "wd_server_add_gauge: " + m);
+  }
+  {
+    cudaError_t e = cudaMalloc(&pl.pf_buf, (size_t)2 * c.g.Vh * 24 * 8);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl.pf_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl.pf_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl.pf_free, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(pl.pf_free, st);  // the buffer starts free
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (pl.pf_free) cudaEventDestroy(pl.pf_free);
+      if (pl.pf_done) cudaEventDestroy(pl.pf_done);
+      if (pl.pf_stream) cudaStreamDestroy(pl.pf_stream);
+      if (pl.pf_buf) cudaFree(pl.pf_buf);
+      wd_destroy(pl.ctx);
+      cudaStreamDestroy(st);
+      return serr(s, e == cudaErrorMemoryAllocation ? WD_ERR_OOM : WD_ERR_CUDA,
+                  std::string("wd_server_add_gauge: prefetch buffer: ") + cudaGetErrorString(e));
+    }
   }
   s->used += pl.fixed_bytes;
   s->pools.push_back(std::move(pl));
