@@ -44,6 +44,7 @@ struct Geom {
   int XhY, XhYZ;      // even-odd index steps in y, z (t step is XhYZ)
   int wy, wz, wt;     // index jumps of the periodic wrap in y, z, t
   FastDiv dXh, dY, dZ;
+  int h_begin, h_end;  // output sites of a dslash launch: [h_begin, h_end) (0, Vh: all)
 };
 
 inline Geom make_geom(const int dims[4], int tbc_anti) {
@@ -66,6 +67,8 @@ inline Geom make_geom(const int dims[4], int tbc_anti) {
   g.dXh = make_fastdiv(g.Xh);
   g.dY = make_fastdiv(g.Y);
   g.dZ = make_fastdiv(g.Z);
+  g.h_begin = 0;
+  g.h_end = g.Vh;
   return g;
 }
 

@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(kDslashBlock, (DslashOccupancy<R, In, Epi::NRE
   double red[NR];
 #pragma unroll
   for (int k = 0; k < NR; ++k) red[k] = 0.0;
-  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += gridDim.x * blockDim.x) {
+  for (int h = g.h_begin + blockIdx.x * blockDim.x + threadIdx.x; h < g.h_end; h += gridDim.x * blockDim.x) {
     R acc[24];
     if constexpr (UseAsync<In, R8>::value) dslash_site_async<DAGGER, TFIX>(g, in, gauge, h, parity, acc);
     else dslash_site<DAGGER, TFIX, R8, Epi::NRED == 0>(g, in, gauge, h, parity, acc);
@@ -1115,7 +1115,9 @@ inline int wave_grid(int units, int block, int num_sms, int per_sm) {
 
 template <typename R, class In, class G, class Epi>
 void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int dagger, const Epi& epi,
-                   cudaStream_t s) {
+                   cudaStream_t s, const Geom* sub = nullptr) {
+  // sub: the context's geometry with a narrower output-site range
+  const Geom& geo = sub ? *sub : c.g;
   // FP64 links never use the 8 numbers
   const bool r8 = (sizeof(R) == 4) && c.low_recon == 8;
   auto go = [&](auto dag, auto tfix, auto rec8) {
@@ -1132,8 +1134,8 @@ void launch_dslash(const Ctx& c, const In& in, const G& gauge, int parity, int d
     // 64^3x128) keep 16 blocks per SM.
     constexpr bool kWave = !(sizeof(R) == 8 || (In::kIntCodes && !kTfix));
     static const int per_sm = kWave ? resident_blocks(k, kDslashBlock) : 16;
-    const int grid = wave_grid(c.g.Vh, kDslashBlock, c.num_sms, per_sm);
-    launch_pdl(k, dim3(grid), dim3(kDslashBlock), 0, s, c.g, in, gauge, parity, epi);
+    const int grid = wave_grid(geo.h_end - geo.h_begin, kDslashBlock, c.num_sms, per_sm);
+    launch_pdl(k, dim3(grid), dim3(kDslashBlock), 0, s, geo, in, gauge, parity, epi);
   };
   using T_ = std::true_type;
   using F_ = std::false_type;
@@ -1340,6 +1342,21 @@ struct Impl {
   static void slab_dslash(const Ctx& c, void* out, const void* in, const void* halo_lo, const void* halo_hi,
                           const void* link_halo, int flip_lo, int flip_hi, int parity, int dagger, int region,
                           cudaStream_t s) {
+    // the interior slices need no halo: the whole-lattice kernel (cp.async
+    // pipeline, spin-paired hops) over their site range; region 2 is the
+    // interior launch followed by the boundary one, so that it writes what
+    // regions 0 and 1 write
+    if (region == 0 || region == 2) {
+      Geom sub = c.g;
+      sub.h_begin = c.g.XhYZ;
+      sub.h_end = c.g.XhYZ * (c.g.T - 1);
+      if (sub.h_end > sub.h_begin) {
+        EpiStore<S> e{T::view(out, c.g)};
+        launch_dslash<R>(c, T::view(in, c.g), T::gauge(c), parity, dagger, e, s, &sub);
+      }
+      if (region == 0) return;
+      region = 1;
+    }
     const int fs = face_stride(c.g);
     const SlabRegion reg{region, c.g.XhYZ, c.g.T, c.g.Vh};
     const int n = reg.count();
