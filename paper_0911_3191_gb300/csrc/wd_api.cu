@@ -596,7 +596,13 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
   // |b|^2 (both parities), b_hat = b_e + kappa D_eo b_o, |b_hat|^2
   o64->norm2(c, c.scalars + 0, b_e, s);
   o64->norm2(c, c.scalars + 1, b_o, s);
-  o64->dslash_xpay(c, sb.b_hat, b_o, b_e, kappa, nullptr, 0, 0, s);
+  // a source without odd sites (an even-site point source) has b_hat = b_e
+  // exactly: its D_eo b_o is skipped
+  WD_CK(ctx, cudaMemcpyAsync(c.host_pinned + 1, c.scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  WD_CK(ctx, cudaStreamSynchronize(s));
+  const bool odd_zero = c.host_pinned[1] == 0.0;
+  if (odd_zero) WD_CK(ctx, cudaMemcpyAsync(sb.b_hat, b_e, f64, cudaMemcpyDeviceToDevice, s));
+  else o64->dslash_xpay(c, sb.b_hat, b_o, b_e, kappa, nullptr, 0, 0, s);
   o64->norm2(c, c.scalars + 2, sb.b_hat, s);
   const void* setup_src = sb.b_hat;
   if (x0) {
@@ -715,7 +721,7 @@ wd_status solve_device(wd_ctx* ctx, void* x_full, const void* b_full, double kap
     // and the even residual dslash
     // (an initial guess: its two residual dslashes instead of the zeroing,
     // and the control update when it already meets the tolerance)
-    const long long setup = 3 + 1 + (x0 ? 2 : 1) + 1 + 4 + (start_converged ? 1 : 0);
+    const long long setup = 3 + (odd_zero ? 0 : 1) + (x0 ? 2 : 1) + 1 + 4 + (start_converged ? 1 : 0);
     const long long per_it = (p.solver == WD_BICGSTAB ? 7 : 5) + (p.use_graph ? 1 : 0);
     const long long per_up = (p.solver == WD_BICGSTAB) ? (p.inner_precision == WD_F64 ? 4 : 5) : 5;
     info->kernel_launches = setup + (long long)hc.iter * per_it + (long long)hc.updates * per_up + 2;
