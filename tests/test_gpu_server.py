@@ -167,3 +167,34 @@ def test_rhs_tile_refused():
     import paper_0911_3191_gb300 as m
     with pytest.raises(m.WDError):
         m.Server(rhs_tile=3)
+
+
+def test_step_trace_and_prefetched_sources(fields, tmp_path, monkeypatch):
+    """With WD_SERVER_TRACE set, the server writes one CSV row per step on
+    destroy; with one slot and a queue, every source after the first is
+    uploaded ahead (prefetch buffer) and every result still reaches its
+    tolerance (checked by the oracle)."""
+    import csv
+    import paper_0911_3191_gb300 as m
+    trace = tmp_path / "trace.csv"
+    monkeypatch.setenv("WD_SERVER_TRACE", str(trace))
+    dims = (8, 8, 8, 16)
+    U = fields[dims]
+    srv = m.Server(max_slots=1, iters_per_step=4, inner_precision=m.Q16)
+    gid = srv.add_gauge(dims, U)
+    bs = [li.gaussian_spinor(dims, 2600 + k) for k in range(4)]
+    ids = [srv.submit(gid, b, 0.12, 1e-10) for b in bs]
+    order = list(ids)
+    done = _drain(srv, ids)
+    steps = srv.stats()["steps"]
+    srv.close()
+    for rid, b in zip(order, bs):
+        res, x = done[rid]
+        assert res.status == 0 and oracle.true_residual(x, b, U, dims, 0.12) <= 1e-10
+    lines = trace.read_text().splitlines()
+    assert lines[0].startswith("# host buffers page-locked")
+    rows = list(csv.DictReader(lines[1:]))
+    assert len(rows) == steps
+    assert sum(int(r["admitted"]) for r in rows) == 4
+    assert all(r["dims"] == "8x8x8x16" and int(r["capacity"]) == 1 for r in rows)
+    assert all(float(r["t_end_s"]) >= float(r["t_launch_s"]) > 0.0 for r in rows)
