@@ -407,6 +407,30 @@ def run_ours(args):
             e2e_t.append(dt)
         assert r.status == 0
     e2e_value = ws * len(e2e_t) / max_over_ranks(ws, sum(e2e_t))
+    # the host link alone: the same bytes copied each way between the same
+    # pinned buffers and a device array, timed with CUDA events, so that the
+    # end-to-end overhead splits into the copies and the library's own work
+    dev = torch.empty(bh.numel(), dtype=bh.dtype, device="cuda")
+    cs = torch.cuda.Stream()
+    h2d_ms, d2h_ms = [], []
+    with torch.cuda.stream(cs):
+        for k in range(4):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(cs)
+            dev.copy_(bh, non_blocking=True)
+            ev[1].record(cs)
+            xh.copy_(dev, non_blocking=True)
+            ev[2].record(cs)
+            ev[2].synchronize()
+            if k > 0:
+                h2d_ms.append(ev[0].elapsed_time(ev[1]))
+                d2h_ms.append(ev[1].elapsed_time(ev[2]))
+    del dev
+    nbytes = bh.numel() * bh.element_size()
+    host_link = {"h2d_GB_per_s": round(nbytes / statistics.mean(h2d_ms) / 1e6, 1),
+                 "d2h_GB_per_s": round(nbytes / statistics.mean(d2h_ms) / 1e6, 1),
+                 "copies_ms": round(statistics.mean(h2d_ms) + statistics.mean(d2h_ms), 3),
+                 "e2e_minus_device_ms": round(1000.0 * ws / e2e_value - 1000.0 * t_total / args.steps, 3)}
 
     # ---- rooflines.  The dominant kernel of the step is the FP64 dslash of the
     # reliable updates (about 60% of the solve by the host-loop launch list),
@@ -451,7 +475,7 @@ def run_ours(args):
             "speedup_vs_fp64": round(f64_s / (t_total / args.steps), 3),
             "solve_by_inner_precision": by_inner,
             "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": V * 24 * 8,
-                    "d2h_bytes_per_step": V * 24 * 8},
+                    "d2h_bytes_per_step": V * 24 * 8, "host_link": host_link},
             "gpu_launches": launches, "roofline": roofline, "dslash_roofline": dslash_roofline, "clocks": clocks}
 
     # ---- dslash bandwidth sweep on the large lattice (inputs >> L2)
